@@ -1,0 +1,147 @@
+"""Pins of the oracle's coupled behaviour: symmetries and balance laws the
+method must keep, and the paper's own statements about the convection cases
+(section 3.2: Eq. 7 and Table 1, and the qualitative findings reported with
+Figs. 4 and 5)."""
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+
+def _conv(orc, shape, face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0):
+    return orc.Oracle(*shape, face=face, Ra=Ra, Pr=Pr, Ste=Ste, Ma=Ma, s0=s0, derive=True)
+
+
+def test_side_heated_mirror_symmetry(orc):
+    """x -> nx-1-x maps the side-heated cavity onto itself."""
+    o = _conv(orc, (9, 14, 12))
+    o.step(300)
+    T, u, s, lf = o.get()
+    assert np.abs(u).max() > 1e-3  # convection is running
+    np.testing.assert_allclose(T, T[:, :, ::-1], atol=1e-12)
+    np.testing.assert_allclose(u[..., 0], -u[:, :, ::-1, 0], atol=1e-12)
+    np.testing.assert_allclose(u[..., 1:], u[:, :, ::-1, 1:], atol=1e-12)
+    np.testing.assert_allclose(s, s[:, ::-1], atol=1e-12)
+
+
+def test_bottom_heated_mirror_symmetry(orc):
+    """Heated from z = 0 the cavity is symmetric under both x and y mirrors."""
+    o = _conv(orc, (8, 10, 14), face=1)
+    o.step(200)
+    T, u, s, lf = o.get()
+    np.testing.assert_allclose(T, T[:, :, ::-1], atol=1e-12)
+    np.testing.assert_allclose(T, T[:, ::-1, :], atol=1e-12)
+    np.testing.assert_allclose(u[..., 0], -u[:, :, ::-1, 0], atol=1e-12)
+    np.testing.assert_allclose(u[..., 1], -u[:, ::-1, :, 1], atol=1e-12)
+    np.testing.assert_allclose(s, s[::-1, ::-1], atol=1e-12)
+
+
+def test_liquid_mass_conserved_while_melting(orc):
+    """Bounce-back conserves mass and each melted node enters at rho0 = 1, so
+    sum(rho over liquid) - (number of liquid nodes) stays at its initial value."""
+    o = _conv(orc, (8, 12, 10), Ste=1.0)
+    i0 = o.info()
+    o.step(400)
+    i1 = o.info()
+    assert i1["n_liquid"] > i0["n_liquid"]
+    assert (i1["mass"] - i1["n_liquid"]) == pytest.approx(i0["mass"] - i0["n_liquid"], abs=1e-10)
+
+
+def test_energy_balance_conduction(orc):
+    """Heat in through the isothermal walls = sensible heat gained by the
+    liquid + latent heat (Th - Tm)/Ste of the melted volume (Tm = 0, so the
+    solid holds no sensible heat).  First-order consistent: a small imbalance
+    that shrinks with refinement."""
+    rel = []
+    for n in (16, 32):
+        o = orc.Oracle(2, n, 2, Ra=0, Ste=0.5, s_nu=1 / 0.8, s_alpha=2 / 3)
+        i0 = o.info(); lf0 = o.get()[3]
+        o.step(int(1000 * (n / 32) ** 2))
+        i1 = o.info(); lf1 = o.get()[3]
+        q = i1["q_hot"] + i1["q_cold"]
+        sensible = i1["sum_T_liquid"] - i0["sum_T_liquid"]
+        latent = (1.0 / 0.5) * (lf1 - lf0) * n * 4
+        rel.append(abs(q - sensible - latent) / q)
+    assert rel[0] < 0.02 and rel[1] < rel[0]
+
+
+def test_fourier_number_eq7(orc):
+    """Eq. 7 with c = sqrt(3) c_s = 1 equals alpha t / H^2 for the lattice
+    parameters derived from Ra, Pr and Ma; Table 1's two cases are then shown
+    at the same lattice time (Fo 1.00 for Ra 25000 equals Fo 1.57 for
+    Ra 10000, section 3.2)."""
+    cases = load_golden("table1_convection_cases.txt")
+    H, Ma = 32, 0.1
+    times = []
+    for case, Pr, Ra, Ste, Fo_shown in cases:
+        o = orc.Oracle(4, H, 4, Ra=Ra, Pr=Pr, Ste=Ste, Ma=Ma, derive=True)
+        a = o.info()["alpha"]
+        t = 1234.0
+        fo_eq7 = t * 1.0 / H * Ma / np.sqrt(3 * Ra * Pr)
+        assert a * t / H ** 2 == pytest.approx(fo_eq7, rel=1e-13)
+        times.append(Fo_shown * H ** 2 / a)
+    assert times[0] == pytest.approx(times[1], rel=0.01)
+
+
+def test_convection_findings(orc):
+    """Section 3.2 with Fig. 4: the liquid warms with height, the hot fluid
+    rises along the heated wall, and the front advances faster at the top."""
+    o = _conv(orc, (10, 18, 18), s0=4.0)
+    o.step(1200)
+    T, u, s, lf = o.get()
+    z = np.arange(18)
+    Tliq = T[:, 2, :].mean(axis=1)             # near the heated wall, over x
+    assert np.corrcoef(z, Tliq)[0, 1] > 0.8
+    assert u[9, 0, 5, 2] > 0                   # upward at mid height next to the wall
+    front = s.mean(axis=1)                     # s(z) averaged over x
+    assert front[-3:].mean() > front[:3].mean() + 1.0
+
+
+def test_lower_rayleigh_melts_slower(orc):
+    """Section 3.2 / conclusion: at equal Fo a lower Ra gives a smaller liquid
+    fraction (pure conduction would give the same one)."""
+    lfs = []
+    for Ra in (1e5, 1e4):
+        o = _conv(orc, (8, 16, 16), Ra=Ra, s0=2.0)
+        info = o.info()
+        Fo_end = 0.25
+        steps = int(round(Fo_end * 16 ** 2 / info["alpha"] - info["t0"]))
+        o.step(steps)
+        lfs.append(o.get()[3])
+    assert lfs[0] > lfs[1] + 0.01
+
+
+@pytest.mark.parametrize("face,axis", [(0, "x"), (0, "z"), (1, "x"), (1, "y")])
+def test_tilted_front_moves_along_its_normal(orc, face, axis):
+    """Eq. 6 geometry: a planar front a = s tilted by slope m along one
+    in-plane axis, in a linear temperature field of gradient magnitude b with
+    T = Tm on the front, advances along its normal at alpha Ste/(Th - Tm) b,
+    i.e. ds/dt is that times sqrt(1 + m^2) -- what the (1 + s_x^2 + s_z^2)
+    factor of Eq. 6 gives with dT/da = -b / sqrt(1 + m^2).  Interior columns
+    only (the mirror ghost halves the slope at the side walls)."""
+    m, b, s0, H, L, W = 0.4, 0.2, 6.0, 16, 8, 3
+    # (nx, ny, nz) with the heating axis of length H, the tilt axis of length L
+    dims = {"x": 0, "y": 1, "z": 2}
+    heat = 1 if face == 0 else 2
+    size = [W, W, W]
+    size[heat] = H
+    size[dims[axis]] = L
+    o = orc.Oracle(*size, face=face, Ra=0, Ste=0.5, s_nu=1 / 0.8, s_alpha=1.0)
+    e, w, _ = orc.lattice19()
+    e7, w7, _ = orc.lattice7()
+    nz, ny, nx = o.shape
+    Z, Y, X = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    coord = {"x": X, "y": Y, "z": Z}
+    a = Y if face == 0 else Z
+    sfield = s0 + m * (coord[axis] - L / 2)
+    T = b * (sfield - a) / np.sqrt(1 + m * m)
+    # the front heights per column, in the oracle's column order (rows: the
+    # second in-plane axis, columns: x)
+    s_cols = sfield[:, 0, :] if face == 0 else sfield[0, :, :]
+    o.set_state(np.tile(w[:, None], (1, o.N)), w7[:, None] * T.reshape(1, -1), s_cols.ravel())
+    o.step(1)
+    s1 = o.get()[2]
+    speed = o.info()["alpha"] * 0.5 / 1.0 * b * np.sqrt(1 + m * m)
+    ds = s1 - s_cols
+    inner = ds[:, 1:-1] if axis == "x" else ds[1:-1, :]
+    np.testing.assert_allclose(inner, speed, rtol=1e-6)
