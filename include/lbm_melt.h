@@ -1,0 +1,171 @@
+/*
+ * lbm_melt.h -- C ABI of the GB300 (sm_103a) double-MRT lattice Boltzmann
+ * library for 3-D melting with interfacial tracking.
+ *
+ * Method: Li, Yang & Zhang, "Lattice Boltzmann method simulation of 3-D
+ * melting using double MRT model with interfacial tracking method",
+ * arXiv:1604.03478 -- section 1 (problem statement: a cubic cavity of edge H
+ * heated to Th on one wall, the opposite wall at Tc <= Tm, the others
+ * adiabatic, no-slip everywhere), section 2 (Eqs. 1-3: D3Q19 MRT flow with a
+ * body force; Eqs. 4-5: D3Q7 MRT energy; Eq. 6: the front velocity from the
+ * interface energy balance) and Eq. 7 (Fourier number).
+ *
+ * Conventions
+ *   - Every call returns an lbm_status; nothing throws across the ABI.  On an
+ *     error, lbm_melt_last_error() gives a message.
+ *   - Node (x, y, z), 0 <= x < nx etc., has its centre at (x+1/2, y+1/2,
+ *     z+1/2); the walls are at 0 and n on each axis.  Per-node arrays are
+ *     row-major (z, y, x) with x fastest: index (z*ny + y)*nx + x.
+ *   - The heating axis a is y (heated_face 0: heated wall y = 0) or z
+ *     (heated_face 1: heated wall z = 0); gravity is always -z.  The front is
+ *     a height field s over the two other axes ("columns"): column index
+ *     z*nx + x for heated_face 0, y*nx + x for heated_face 1.  Node j of a
+ *     column is liquid iff j + 1/2 < s.
+ *   - ptr_kind 0: host pointers; 1: device pointers (on the handle's device).
+ *     Outputs are caller-owned.  The handle owns all of its device memory.
+ *   - lbm_melt_step is asynchronous on the handle's stream; a front that
+ *     moved more than half a cell in a step (LBM_EUNSTABLE) or a non-finite
+ *     temperature (LBM_ENAN) is reported by the next call that synchronises
+ *     (lbm_melt_get, lbm_melt_get_state, lbm_melt_sync).
+ */
+#ifndef LBM_MELT_H
+#define LBM_MELT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_melt lbm_melt; /* opaque handle */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* an argument is out of range */
+    LBM_ENOMEM = -2,    /* device or host allocation failed */
+    LBM_ECUDA = -3,     /* a CUDA call failed (message in last_error) */
+    LBM_EUNSTABLE = -4, /* the front moved more than half a cell in one step */
+    LBM_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    LBM_ENAN = -6       /* a non-finite temperature reached the front */
+} lbm_status;
+
+/* Cavity and storage.  heated_face: 0 = wall y = 0 (side-heated), 1 = wall
+   z = 0 (bottom-heated).  precision: 0 = FP32 storage, 1 = FP16 storage of
+   the shifted distributions f - w rho0 and g - w Tm (FP32 arithmetic in both;
+   the front and the reductions in FP64).  Ma: Mach number U0 / c_s (Eq. 7;
+   any value below 0.3).  s0: initial front height above the heated wall in
+   lattice units (0 selects 1.0); the liquid below it starts at the analytic
+   conduction-melting temperature of that front, at rest. */
+typedef struct {
+    int nx, ny, nz;
+    int heated_face;
+    int precision;
+    double Ma;
+    double s0;
+} lbm_melt_grid;
+
+/* Relaxation rates (Eqs. 2 and 4).  D3Q19 (moment basis of d'Humieres et al.
+   2002): s_nu on the five viscous-stress moments, s_e energy, s_eps energy
+   square, s_q heat flux, s_pi the two 4th-order stress moments, s_m the three
+   3rd-order moments.  D3Q7: s_alpha on the three flux moments (alpha =
+   (1/s_alpha - 1/2)/4), s_g4 and s_g5 on the higher ones.  derive_from_Ra = 1:
+   s_nu and s_alpha follow from Ra, Pr, Ma and the cavity length H along the
+   heating axis (nu = Ma/sqrt(3) H sqrt(Pr/Ra), alpha = nu/Pr); 0: as given.
+   In both cases g*beta = Ra nu alpha / ((Th - Tm) H^3), zero for Ra = 0.
+   A rate <= 0 among s_e .. s_m, s_g4, s_g5 selects its default (1.19, 1.4,
+   1.2, 1.4, 1.98, 1, 1). */
+typedef struct {
+    double s_nu, s_e, s_eps, s_q, s_pi, s_m;
+    double s_alpha, s_g4, s_g5;
+    int derive_from_Ra;
+} lbm_melt_rates;
+
+/* Derived lattice quantities of a handle (or of a would-be handle, see
+   lbm_melt_derive). */
+typedef struct {
+    double nu, alpha, gbeta;     /* lattice viscosity, diffusivity, g*beta */
+    double tau_nu;               /* 3 nu + 1/2 */
+    double s_nu, s_alpha;        /* rates in effect */
+    double lambda;               /* Neumann root: lambda e^(lambda^2) erf(lambda) = Ste/sqrt(pi) */
+    double t0;                   /* lattice time of the initial front, s0^2 / (4 lambda^2 alpha) */
+    double H;                    /* cavity length along the heating axis */
+    long long n_cells, n_columns;
+    long long steps;             /* steps taken */
+    size_t device_bytes;         /* device memory held by the handle */
+} lbm_melt_info;
+
+/* Validate the arguments and fill *info with the derived lattice parameters,
+   without touching the GPU.  Rejects: a cavity edge < 1 or a heating-axis
+   length < 4, heated_face or precision out of range, Th <= Tm, Tc > Tm,
+   Ste < 0 (Ste = 0 holds the front in place), Ra < 0, Ra = 0 with
+   derive_from_Ra, Ma outside (0, 0.3] when deriving,
+   tau_nu <= 0.5 + 1e-4, any rate outside (0, 2), s0 outside [0.5, H]. */
+lbm_status lbm_melt_derive(const lbm_melt_grid *grid, double Ra, double Pr, double Ste,
+                           double Th, double Tc, double Tm, const lbm_melt_rates *rates,
+                           lbm_melt_info *info);
+
+/* The message explaining why lbm_melt_derive rejects these arguments ("" if
+   it accepts them).  Returns a static buffer (not thread-safe). */
+const char *lbm_melt_derive_error(const lbm_melt_grid *grid, double Ra, double Pr, double Ste,
+                                  double Th, double Tc, double Tm, const lbm_melt_rates *rates);
+
+/* Create a cavity on the current CUDA device, in its initial state.
+   cuda_stream: the cudaStream_t the handle launches on (NULL: the legacy
+   default stream).  On success *out receives the handle; on failure *out is
+   NULL and the status says why (the message is lost with the handle: use
+   lbm_melt_derive to see validation messages). */
+lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double Pr, double Ste,
+                           double Th, double Tc, double Tm, const lbm_melt_rates *rates,
+                           void *cuda_stream, lbm_melt **out);
+
+/* Advance n >= 0 time steps (Eqs. 1-6 per step: stream-collide, front
+   update, phase flip).  Asynchronous. */
+lbm_status lbm_melt_step(lbm_melt *h, long long n);
+
+/* Macroscopic outputs, any of them NULL to skip: T per node (solid nodes
+   report Tm), u per node as 3 interleaved floats (force-shifted velocity,
+   zero in solid nodes), S per column (the front height above the heated
+   wall), liquid_fraction = sum(S) / (H * columns).  Synchronises. */
+lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
+                        int ptr_kind);
+
+/* Distributions in natural form (post-streaming, pre-collision; f_i and g_i,
+   not shifted), direction-major: f[i*N + node], g[i*N + node]; solid nodes
+   report f = 0.  Any pointer may be NULL.  Synchronises. */
+lbm_status lbm_melt_get_state(lbm_melt *h, float *f, float *g, double *S, int ptr_kind);
+
+/* Replace the state with natural-form distributions and front heights (same
+   layout as lbm_melt_get_state; f of solid nodes is ignored).  f or g may be
+   NULL to keep that part; a new S needs both f and g.  The phase flags and
+   the ghost nodes are recomputed from the new state. */
+lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *g, const double *S,
+                              int ptr_kind);
+
+/* Heated-wall temperature per column (overrides the scalar Th on the wall;
+   the scalar Th still defines the Stefan number).  Takes effect for the
+   next step's streaming. */
+lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, int ptr_kind);
+
+/* Derived quantities and counters of a handle. */
+lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info);
+
+/* Wait for the handle's stream; report a device-side error flag. */
+lbm_status lbm_melt_sync(lbm_melt *h);
+
+/* Kernel timing: when enabled, each stream-collide launch is bracketed by
+   CUDA events; lbm_melt_kernel_time returns (after synchronising) the summed
+   milliseconds and the number of timed launches since the last reset. */
+lbm_status lbm_melt_set_timing(lbm_melt *h, int enable);
+lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, int reset);
+
+const char *lbm_melt_last_error(const lbm_melt *h);
+void lbm_melt_destroy(lbm_melt *h);
+
+/* Library version string. */
+const char *lbm_melt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_MELT_H */

@@ -766,10 +766,11 @@ void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s
     refresh_ghosts(S);
 }
 
-/* Heated-wall temperature per column (overrides the scalar Th at the wall). */
+/* Heated-wall temperature per column (overrides the scalar Th at the wall).
+   It takes effect at the next step's streaming; the ghost nodes of the
+   current state were prepared with the field of the step that produced it. */
 void orc_set_hot_wall(orc_sim *S, const double *Thw) {
     memcpy(S->Thw, Thw, sizeof(double) * S->ncols);
-    refresh_ghosts(S);
 }
 
 /* info[0..]: nu, alpha, gbeta, lambda, t0, s_nu, s_alpha, H, steps, q_hot,

@@ -1,0 +1,143 @@
+"""Convenience wrapper of one cavity handle of the C ABI.
+
+Every method is argument marshalling around one ``lbm_melt_*`` call.  Host
+results come back as numpy arrays; ``get_device`` returns torch CUDA tensors
+filled by the library through device pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+
+DEFAULT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98, s_g4=1.0, s_g5=1.0)
+
+
+def default_rates():
+    return dict(DEFAULT_RATES)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_abi.STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def make_args(nx, ny, nz, face=0, precision=0, Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, **rates):
+    r = dict(DEFAULT_RATES)
+    r.update(rates)
+    grid = _abi.lbm_melt_grid(nx, ny, nz, face, precision, Ma, s0)
+    rr = _abi.lbm_melt_rates(s_nu, r["s_e"], r["s_eps"], r["s_q"], r["s_pi"], r["s_m"], s_alpha,
+                             r["s_g4"], r["s_g5"], 1 if derive else 0)
+    return grid, rr
+
+
+class Cavity:
+    """One cavity on the current CUDA device.
+
+    Arguments follow ``lbm_melt_create``: the grid (nx, ny, nz), heated face
+    (0: y = 0, 1: z = 0), storage precision (0 fp32, 1 fp16), Ma, initial
+    front s0, Ra, Pr, Ste, Th, Tc, Tm and the rates (``derive`` takes s_nu,
+    s_alpha from Ra, Pr, Ma and H).  ``stream`` is a cudaStream_t as int
+    (default: torch's current stream).
+    """
+
+    def __init__(self, nx, ny, nz, face=0, precision=0, Ra=0.0, Pr=1.0, Ste=0.1, Th=1.0, Tc=0.0, Tm=0.0,
+                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, stream=None, **rates):
+        L = _abi.load()
+        self.grid, self.rates = make_args(nx, ny, nz, face, precision, Ma, s0, s_nu, s_alpha, derive, **rates)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        st = L.lbm_melt_create(C.byref(self.grid), Ra, Pr, Ste, Th, Tc, Tm, C.byref(self.rates),
+                               C.c_void_p(stream), C.byref(h))
+        if st != 0:
+            msg = L.lbm_melt_derive_error(C.byref(self.grid), Ra, Pr, Ste, Th, Tc, Tm, C.byref(self.rates))
+            raise LbmError(st, (msg or b"").decode() or "lbm_melt_create failed")
+        self._h = h
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.face = face
+        self.H = ny if face == 0 else nz
+        self.cols_shape = (nz, nx) if face == 0 else (ny, nx)
+        self.ncols = self.cols_shape[0] * self.cols_shape[1]
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.load().lbm_melt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise LbmError(st, _abi.load().lbm_melt_last_error(self._h).decode())
+
+    # -- calls
+    def step(self, n=1):
+        self._check(_abi.load().lbm_melt_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(_abi.load().lbm_melt_sync(self._h))
+
+    def get(self, T=True, u=True, S=True, lf=True):
+        Ta = np.zeros(self.shape, np.float32) if T else None
+        ua = np.zeros(self.shape + (3,), np.float32) if u else None
+        Sa = np.zeros(self.cols_shape, np.float64) if S else None
+        la = np.zeros(1, np.float64) if lf else None
+        self._check(_abi.load().lbm_melt_get(self._h, _ptr(Ta), _ptr(ua), _ptr(Sa), _ptr(la), 0))
+        return Ta, ua, Sa, (float(la[0]) if lf else None)
+
+    def get_device(self, T=None, u=None, S=None, lf=None):
+        """Fill caller-owned torch CUDA tensors (any may be None)."""
+        self._check(_abi.load().lbm_melt_get(self._h, _ptr(T), _ptr(u), _ptr(S), _ptr(lf), 1))
+
+    def get_state(self):
+        f = np.zeros((19, self.N), np.float32)
+        g = np.zeros((7, self.N), np.float32)
+        s = np.zeros(self.ncols, np.float64)
+        self._check(_abi.load().lbm_melt_get_state(self._h, _ptr(f), _ptr(g), _ptr(s), 0))
+        return f, g, s
+
+    def set_state(self, f=None, g=None, s=None):
+        f = None if f is None else np.ascontiguousarray(f, np.float32).reshape(19, self.N)
+        g = None if g is None else np.ascontiguousarray(g, np.float32).reshape(7, self.N)
+        s = None if s is None else np.ascontiguousarray(s, np.float64).reshape(self.ncols)
+        self._check(_abi.load().lbm_melt_set_state(self._h, _ptr(f), _ptr(g), _ptr(s), 0))
+
+    def set_hot_wall(self, Thw, ptr_kind=None):
+        if ptr_kind is None:
+            ptr_kind = 0 if isinstance(Thw, np.ndarray) else 1
+        if ptr_kind == 0:
+            Thw = np.ascontiguousarray(Thw, np.float32).reshape(self.ncols)
+        self._check(_abi.load().lbm_melt_set_hot_wall(self._h, _ptr(Thw), ptr_kind))
+
+    def info(self):
+        i = _abi.lbm_melt_info()
+        self._check(_abi.load().lbm_melt_get_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def set_timing(self, on=True):
+        self._check(_abi.load().lbm_melt_set_timing(self._h, 1 if on else 0))
+
+    def kernel_time(self, reset=True):
+        ms = C.c_double()
+        n = C.c_longlong()
+        self._check(_abi.load().lbm_melt_kernel_time(self._h, C.byref(ms), C.byref(n), 1 if reset else 0))
+        return ms.value, n.value

@@ -1,0 +1,41 @@
+// launch.h -- host-side launchers of the kernels, one instantiation per
+// storage type (k_f32.cu: float, k_f16.cu: __half).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_core.cuh"
+
+namespace lbm {
+
+struct Bufs {
+    void *F, *G;                 // shifted distributions, 19 and 7 arrays of ld elements
+    const int *js;               // liquid-node count per column (current flags)
+    int *js_next;
+    const double *s;             // front per column (current)
+    double *s_next;
+    float *gpost;                // ghost-node post-collision g, 7 x ncols
+    const float *thw_rd, *thw_wr;
+    int *status;
+};
+
+template <typename ST> struct Launch {
+    static cudaError_t stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st);
+    static cudaError_t front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st);
+    static cudaError_t flip(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st);
+    static cudaError_t macro(const KP &p, int face, int inflight, const Bufs &b, float *T, float *u, cudaStream_t st);
+    static cudaError_t state_out(const KP &p, int face, int inflight, const Bufs &b, float *f, float *g, cudaStream_t st);
+    static cudaError_t state_in(const KP &p, int face, const Bufs &b, const float *f, const float *g, cudaStream_t st);
+    static cudaError_t init(const KP &p, int face, const Bufs &b, const float *Tprof, cudaStream_t st);
+};
+
+// Block shape for the per-node kernels: 128 threads, x-major.
+inline dim3 node_block(const KP &p) {
+    int bx = p.nx >= 128 ? 128 : (p.nx > 64 ? 128 : (p.nx > 32 ? 64 : 32));
+    return dim3(bx, 128 / bx, 1);
+}
+inline dim3 node_grid(const KP &p, dim3 b) {
+    return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+}
+
+}  // namespace lbm

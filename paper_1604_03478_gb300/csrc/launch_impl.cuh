@@ -1,0 +1,80 @@
+// launch_impl.cuh -- definitions of Launch<ST>; included by exactly one
+// translation unit per storage type.
+#pragma once
+
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace lbm {
+
+template <typename ST>
+cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
+    dim3 grd = node_grid(p, blk);
+    ST *F = (ST *)b.F, *G = (ST *)b.G;
+    if (face == 0) {
+        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost, b.thw_rd, b.thw_wr);
+        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost);
+    } else {
+        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost, b.thw_rd, b.thw_wr);
+        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost);
+    }
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st) {
+    dim3 blk(128), grd((p.ncols + 127) / 128);
+    const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
+    if (face == 0)
+        k_front<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status);
+    else
+        k_front<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st) {
+    dim3 blk(128), grd((p.ncols + 127) / 128);
+    ST *F = (ST *)b.F;
+    if (face == 0) k_flip<ST, 0><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, inflight);
+    else k_flip<ST, 1><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, inflight);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::macro(const KP &p, int face, int inflight, const Bufs &b, float *T, float *u, cudaStream_t st) {
+    dim3 blk = node_block(p), grd = node_grid(p, blk);
+    const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
+    if (face == 0) k_macro<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, T, u);
+    else k_macro<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, T, u);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::state_out(const KP &p, int face, int inflight, const Bufs &b, float *f, float *g, cudaStream_t st) {
+    dim3 blk = node_block(p), grd = node_grid(p, blk);
+    const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
+    if (face == 0) k_state_out<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, f, g);
+    else k_state_out<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, f, g);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::state_in(const KP &p, int face, const Bufs &b, const float *f, const float *g, cudaStream_t st) {
+    dim3 blk = node_block(p), grd = node_grid(p, blk);
+    ST *F = (ST *)b.F, *G = (ST *)b.G;
+    if (face == 0) k_state_in<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, f, g);
+    else k_state_in<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, f, g);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::init(const KP &p, int face, const Bufs &b, const float *Tprof, cudaStream_t st) {
+    dim3 blk = node_block(p), grd = node_grid(p, blk);
+    ST *F = (ST *)b.F, *G = (ST *)b.G;
+    if (face == 0) k_init<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, Tprof);
+    else k_init<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, Tprof);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

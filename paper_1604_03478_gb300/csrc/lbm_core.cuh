@@ -1,0 +1,296 @@
+// lbm_core.cuh -- lattice constants, kernel parameters and the per-node
+// double-MRT collision (Li, Yang & Zhang, arXiv:1604.03478, Eqs. 1-5).
+//
+// Storage convention: every distribution is held SHIFTED by its rest
+// equilibrium, fh_i = f_i - w_i rho0 (rho0 = 1) and gh_i = g_i - w_i Tm, so
+// that a liquid node at rest and a solid node at Tm are all zeros and the
+// stored numbers are small (FP16 storage keeps its precision for them).
+// Arrays are direction-major: direction i of node c lives at base[i*ld + c].
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattices
+// D3Q19 velocities in the order printed in Eq. 3: rest, +-x, +-y, +-z, then
+// the xy, xz and yz diagonals.
+__host__ __device__ constexpr int ex(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int i) {
+    return (i == 3 || i == 7 || i == 8 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 9 || i == 10 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez(int i) {
+    return (i == 5 || i == 11 || i == 12 || i == 15 || i == 16) ? 1
+         : (i == 6 || i == 13 || i == 14 || i == 17 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int e2(int i) { return ex(i) * ex(i) + ey(i) * ey(i) + ez(i) * ez(i); }
+__host__ __device__ constexpr int opp(int i) {
+    int r = 0;
+    for (int j = 0; j < 19; ++j)
+        if (ex(j) == -ex(i) && ey(j) == -ey(i) && ez(j) == -ez(i)) r = j;
+    return r;
+}
+__host__ __device__ constexpr float w19(int i) {
+    return e2(i) == 0 ? 1.0f / 3.0f : (e2(i) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+// D3Q7 velocities in the order of Eq. 5.
+__host__ __device__ constexpr int tx(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__host__ __device__ constexpr int ty(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+__host__ __device__ constexpr int tz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+__host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// w0 = 1/4, so the D3Q7 pseudo sound speed squared is (1 - w0)/3 = 1/4.
+__host__ __device__ constexpr float w7(int i) { return i == 0 ? 0.25f : 0.125f; }
+
+// Row k of the D3Q19 moment basis (d'Humieres et al. 2002) at velocity i;
+// integer-valued on the lattice.
+__host__ __device__ constexpr int mpoly(int k, int i) {
+    const int x = ex(i), y = ey(i), z = ez(i), q = e2(i);
+    return k == 0 ? 1
+         : k == 1 ? 19 * q - 30
+         : k == 2 ? (21 * q * q - 53 * q + 24) / 2
+         : k == 3 ? x
+         : k == 4 ? (5 * q - 9) * x
+         : k == 5 ? y
+         : k == 6 ? (5 * q - 9) * y
+         : k == 7 ? z
+         : k == 8 ? (5 * q - 9) * z
+         : k == 9 ? 3 * x * x - q
+         : k == 10 ? (3 * q - 5) * (3 * x * x - q)
+         : k == 11 ? y * y - z * z
+         : k == 12 ? (3 * q - 5) * (y * y - z * z)
+         : k == 13 ? x * y
+         : k == 14 ? y * z
+         : k == 15 ? x * z
+         : k == 16 ? (y * y - z * z) * x
+         : k == 17 ? (z * z - x * x) * y
+         : (x * x - y * y) * z;
+}
+// |row k|^2; the rows are orthogonal, so M^-1 = M^T diag(1/norm).
+__host__ __device__ constexpr int mnorm(int k) {
+    int s = 0;
+    for (int i = 0; i < 19; ++i) s += mpoly(k, i) * mpoly(k, i);
+    return s;
+}
+
+// Row k of the D3Q7 basis: 1, e_x, e_y, e_z, 6 - 7|e|^2, 3e_x^2 - |e|^2,
+// e_y^2 - e_z^2.
+__host__ __device__ constexpr int npoly(int k, int i) {
+    const int x = tx(i), y = ty(i), z = tz(i), q = x * x + y * y + z * z;
+    return k == 0 ? 1 : k == 1 ? x : k == 2 ? y : k == 3 ? z
+         : k == 4 ? 6 - 7 * q : k == 5 ? 3 * x * x - q : y * y - z * z;
+}
+__host__ __device__ constexpr int nnorm(int k) {
+    int s = 0;
+    for (int i = 0; i < 7; ++i) s += npoly(k, i) * npoly(k, i);
+    return s;
+}
+
+// --------------------------------------------------------- kernel params
+struct KP {
+    int nx, ny, nz;   // cavity
+    int H;            // length along the heating axis
+    int P1, P2;       // column grid: P1 = nx, P2 = nz (face 0) or ny (face 1)
+    int ncols;
+    long long N;      // nodes
+    long long ld;     // distance between direction arrays (elements)
+    float Tm, Tc, gbeta;
+    float s_e, s_eps, s_q, s_nu, s_pi, s_m;
+    float s_alpha, s_g4, s_g5;
+    double Tm_d, Th_d;
+    double coef;      // alpha Ste / (Th - Tm): Eq. 6 front speed per unit -dT/da
+};
+
+// ------------------------------------------------------------ load/store
+template <typename ST> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+// ----------------------------------------------- compile-time transforms
+// acc + sum_i mpoly(K, i) v[i] over the nonzero coefficients only.
+template <int K, int I>
+__device__ __forceinline__ float mrow(const float (&v)[19], float acc) {
+    if constexpr (I == 19) {
+        return acc;
+    } else {
+        constexpr int m = mpoly(K, I);
+        if constexpr (m == 0) return mrow<K, I + 1>(v, acc);
+        else if constexpr (m == 1) return mrow<K, I + 1>(v, acc + v[I]);
+        else if constexpr (m == -1) return mrow<K, I + 1>(v, acc - v[I]);
+        else return mrow<K, I + 1>(v, fmaf((float)m, v[I], acc));
+    }
+}
+
+// acc + sum_k mpoly(k, I) c[k] over k with nonzero coefficients, skipping
+// the rows whose update is identically zero (mass; x and y momentum).
+template <int I, int K>
+__device__ __forceinline__ float mcol(const float (&c)[19], float acc) {
+    if constexpr (K == 19) {
+        return acc;
+    } else {
+        constexpr int m = mpoly(K, I);
+        if constexpr (m == 0 || K == 0 || K == 3 || K == 5) return mcol<I, K + 1>(c, acc);
+        else if constexpr (m == 1) return mcol<I, K + 1>(c, acc + c[K]);
+        else if constexpr (m == -1) return mcol<I, K + 1>(c, acc - c[K]);
+        else return mcol<I, K + 1>(c, fmaf((float)m, c[K], acc));
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void moments_from(const float (&f)[19], float (&m)[19]) {
+    if constexpr (K < 19) {
+        m[K] = mrow<K, 0>(f, -0.0f);
+        moments_from<K + 1>(f, m);
+    }
+}
+
+template <int I>
+__device__ __forceinline__ void add_back(float (&f)[19], const float (&c)[19]) {
+    if constexpr (I < 19) {
+        f[I] = mcol<I, 0>(c, f[I]);
+        add_back<I + 1>(f, c);
+    }
+}
+
+template <int K, int I>
+__device__ __forceinline__ float nrow(const float (&v)[7], float acc) {
+    if constexpr (I == 7) {
+        return acc;
+    } else {
+        constexpr int m = npoly(K, I);
+        if constexpr (m == 0) return nrow<K, I + 1>(v, acc);
+        else if constexpr (m == 1) return nrow<K, I + 1>(v, acc + v[I]);
+        else if constexpr (m == -1) return nrow<K, I + 1>(v, acc - v[I]);
+        else return nrow<K, I + 1>(v, fmaf((float)m, v[I], acc));
+    }
+}
+
+template <int I, int K>
+__device__ __forceinline__ float ncol(const float (&c)[7], float acc) {
+    if constexpr (K == 7) {
+        return acc;
+    } else {
+        constexpr int m = npoly(K, I);
+        if constexpr (m == 0 || K == 0) return ncol<I, K + 1>(c, acc);
+        else if constexpr (m == 1) return ncol<I, K + 1>(c, acc + c[K]);
+        else if constexpr (m == -1) return ncol<I, K + 1>(c, acc - c[K]);
+        else return ncol<I, K + 1>(c, fmaf((float)m, c[K], acc));
+    }
+}
+
+template <int I>
+__device__ __forceinline__ void add_back7(float (&g)[7], const float (&c)[7]) {
+    if constexpr (I < 7) {
+        g[I] = ncol<I, 0>(c, g[I]);
+        add_back7<I + 1>(g, c);
+    }
+}
+
+// -------------------------------------------------------------- collision
+// One liquid node: shifted populations in, shifted post-collision out.
+//   T = Tm + sum gh;  F = g beta (T - Tm) z-hat (Boussinesq, gravity -z);
+//   u = sum fh e + F/2 (rho0 = 1);
+//   D3Q19 (Eq. 2 with the Guo source): m* - m = -S (m - m^eq) + (I - S/2) M F~,
+//   f* = f + M^T D^-1 (m* - m);
+//   D3Q7 (Eq. 4): n* - n = -Q (n - n^eq), n^eq = (T, u T, 3T/4, 0, 0),
+//   g* = g + N^T D^-1 (n* - n).
+// m^eq and M F~ are the closed forms of the incompressible equilibrium and
+// Guo's source for a force along z.  Writes u (for diagnostics) to uout.
+__device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[7], float *uout = nullptr) {
+    float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    const float T = Th + p.Tm;
+    const float Fz = p.gbeta * Th;
+    float m[19];
+    moments_from<0>(f, m);
+    const float rho_h = m[0];
+    const float ux = m[3], uy = m[5], uz = m[7] + 0.5f * Fz;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float uzF = uz * Fz;
+    const float pxx = 2.0f * ux * ux - uy * uy - uz * uz;
+    const float pww = uy * uy - uz * uz;
+    float d[19];
+    d[0] = 0.0f; d[3] = 0.0f; d[5] = 0.0f;
+    d[1] = -p.s_e * (m[1] - (-11.0f * rho_h + 19.0f * uu)) + (1.0f - 0.5f * p.s_e) * (38.0f * uzF);
+    d[2] = -p.s_eps * (m[2] - (3.0f * rho_h - 5.5f * uu)) + (1.0f - 0.5f * p.s_eps) * (-11.0f * uzF);
+    d[4] = -p.s_q * (m[4] + (2.0f / 3.0f) * ux);
+    d[6] = -p.s_q * (m[6] + (2.0f / 3.0f) * uy);
+    d[7] = Fz;
+    d[8] = -p.s_q * (m[8] + (2.0f / 3.0f) * uz) + (1.0f - 0.5f * p.s_q) * (-(2.0f / 3.0f) * Fz);
+    d[9] = -p.s_nu * (m[9] - pxx) + (1.0f - 0.5f * p.s_nu) * (-2.0f * uzF);
+    d[10] = -p.s_pi * (m[10] + 0.5f * pxx) + (1.0f - 0.5f * p.s_pi) * uzF;
+    d[11] = -p.s_nu * (m[11] - pww) + (1.0f - 0.5f * p.s_nu) * (-2.0f * uzF);
+    d[12] = -p.s_pi * (m[12] + 0.5f * pww) + (1.0f - 0.5f * p.s_pi) * uzF;
+    d[13] = -p.s_nu * (m[13] - ux * uy);
+    d[14] = -p.s_nu * (m[14] - uy * uz) + (1.0f - 0.5f * p.s_nu) * (uy * Fz);
+    d[15] = -p.s_nu * (m[15] - ux * uz) + (1.0f - 0.5f * p.s_nu) * (ux * Fz);
+    d[16] = -p.s_m * m[16];
+    d[17] = -p.s_m * m[17];
+    d[18] = -p.s_m * m[18];
+    float c[19];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) c[k] = d[k] * (1.0f / (float)mnorm(k));
+    add_back<0>(f, c);
+
+    float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
+    float n4 = 6.0f * g[0] - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6]);
+    float n5 = 2.0f * (g[1] + g[2]) - (g[3] + g[4] + g[5] + g[6]);
+    float n6 = (g[3] + g[4]) - (g[5] + g[6]);
+    float cn[7];
+    cn[0] = 0.0f;
+    cn[1] = -p.s_alpha * (n1 - ux * T) * (1.0f / (float)nnorm(1));
+    cn[2] = -p.s_alpha * (n2 - uy * T) * (1.0f / (float)nnorm(2));
+    cn[3] = -p.s_alpha * (n3 - uz * T) * (1.0f / (float)nnorm(3));
+    cn[4] = -p.s_g4 * (n4 - 0.75f * Th) * (1.0f / (float)nnorm(4));
+    cn[5] = -p.s_g5 * n5 * (1.0f / (float)nnorm(5));
+    cn[6] = -p.s_g5 * n6 * (1.0f / (float)nnorm(6));
+    add_back7<0>(g, cn);
+    if (uout) { uout[0] = ux; uout[1] = uy; uout[2] = uz; }
+}
+
+// ------------------------------------------------------------- geometry
+template <int FACE> __device__ __forceinline__ int axial(int x, int y, int z) {
+    (void)x;
+    return FACE == 0 ? y : z;
+}
+template <int FACE> __device__ __forceinline__ int column(const KP &p, int x, int y, int z) {
+    return FACE == 0 ? z * p.nx + x : y * p.nx + x;
+}
+// Node of column col at height j.
+template <int FACE> __device__ __forceinline__ void column_node(const KP &p, int col, int j, int &x, int &y, int &z) {
+    x = col % p.nx;
+    int q = col / p.nx;
+    if (FACE == 0) { y = j; z = q; } else { y = q; z = j; }
+}
+__device__ __forceinline__ long long node_index(const KP &p, int x, int y, int z) {
+    return ((long long)z * p.ny + y) * p.nx + x;
+}
+__device__ __forceinline__ bool inside(const KP &p, int x, int y, int z) {
+    return (unsigned)x < (unsigned)p.nx && (unsigned)y < (unsigned)p.ny && (unsigned)z < (unsigned)p.nz;
+}
+template <int FACE> __device__ __forceinline__ bool liquid_at(const KP &p, const int *js, int x, int y, int z) {
+    return inside(p, x, y, z) && axial<FACE>(x, y, z) < __ldg(js + column<FACE>(p, x, y, z));
+}
+
+// Wall crossed by the D3Q7 link that leaves node (x,y,z) along direction i
+// (i.e. x + t_i is outside): 1 heated wall, 2 opposite isothermal wall,
+// 3 adiabatic wall.  Only meaningful when x + t_i is outside.
+template <int FACE> __device__ __forceinline__ int wall_of_link(int i) {
+    // the heating axis is y (directions 3, 4) or z (5, 6); the heated wall is
+    // at coordinate 0, reached going in the negative direction
+    if (FACE == 0) return i == 4 ? 1 : (i == 3 ? 2 : 3);
+    return i == 6 ? 1 : (i == 5 ? 2 : 3);
+}
+
+}  // namespace lbm

@@ -1,0 +1,559 @@
+// lbm_melt.cu -- host side of the C ABI declared in include/lbm_melt.h:
+// argument checking, the lattice parameters of section 1 / Eq. 7, the
+// initial state, device memory, the per-step launch sequence and I/O.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_melt.h"
+#include "launch.h"
+
+#define LBM_API extern "C" __attribute__((visibility("default")))
+
+using lbm::Bufs;
+using lbm::KP;
+
+namespace {
+
+const double CS2T = 0.25;  // D3Q7 pseudo sound speed squared (w0 = 1/4)
+
+struct Derived {
+    int H, P1, P2;
+    long long N, ncols;
+    double nu, alpha, gbeta, s_nu, s_alpha, lambda, t0, s0;
+    double s_e, s_eps, s_q, s_pi, s_m, s_g4, s_g5;
+};
+
+// Root of lambda exp(lambda^2) erf(lambda) = Ste / sqrt(pi) (the one-phase
+// Neumann solution of conduction melting with zero subcooling, section 3.1),
+// by bisection on [0, hi].
+double neumann_lambda(double Ste) {
+    if (!(Ste > 0.0)) return 0.0;
+    const double rhs = Ste / std::sqrt(M_PI);
+    double lo = 0.0, hi = 1.0;
+    while (hi * std::exp(hi * hi) * std::erf(hi) < rhs) hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid * std::exp(mid * mid) * std::erf(mid) < rhs) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+double pick(double v, double dflt) { return v > 0.0 ? v : dflt; }
+
+lbm_status derive(const lbm_melt_grid *g, double Ra, double Pr, double Ste, double Th, double Tc, double Tm,
+                  const lbm_melt_rates *r, Derived &d, char *err, size_t errlen) {
+    auto fail = [&](const char *fmt, ...) {
+        if (err && errlen) {
+            va_list ap;
+            va_start(ap, fmt);
+            vsnprintf(err, errlen, fmt, ap);
+            va_end(ap);
+        }
+        return LBM_EINVAL;
+    };
+    if (!g || !r) return fail("null grid or rates");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail("cavity edges must be >= 1");
+    if (g->heated_face != 0 && g->heated_face != 1) return fail("heated_face must be 0 (y = 0) or 1 (z = 0)");
+    if (g->precision != 0 && g->precision != 1) return fail("precision must be 0 (fp32) or 1 (fp16)");
+    d.H = g->heated_face == 0 ? g->ny : g->nz;
+    d.P1 = g->nx;
+    d.P2 = g->heated_face == 0 ? g->nz : g->ny;
+    if (d.H < 4) return fail("cavity length along the heating axis must be >= 4");
+    d.N = (long long)g->nx * g->ny * g->nz;
+    d.ncols = (long long)d.P1 * d.P2;
+    if (d.N > (1LL << 31) - 1) return fail("too many nodes");
+    if (!(Th > Tm)) return fail("Th must exceed Tm");
+    if (!(Tc <= Tm)) return fail("Tc must not exceed Tm");
+    if (!(Ste >= 0.0)) return fail("Ste must be >= 0");
+    if (!(Ra >= 0.0)) return fail("Ra must be >= 0");
+    if (r->derive_from_Ra) {
+        if (!(Ra > 0.0)) return fail("derive_from_Ra needs Ra > 0");
+        if (!(Pr > 0.0)) return fail("Pr must be > 0");
+        if (!(g->Ma > 0.0 && g->Ma <= 0.3)) return fail("Ma must be in (0, 0.3]");
+        const double U0 = g->Ma / std::sqrt(3.0);
+        d.nu = U0 * d.H * std::sqrt(Pr / Ra);
+        d.alpha = d.nu / Pr;
+        d.s_nu = 1.0 / (3.0 * d.nu + 0.5);
+        d.s_alpha = 1.0 / (d.alpha / CS2T + 0.5);
+    } else {
+        if (!(r->s_nu > 0.0 && r->s_nu < 2.0)) return fail("s_nu must be in (0, 2)");
+        if (!(r->s_alpha > 0.0 && r->s_alpha < 2.0)) return fail("s_alpha must be in (0, 2)");
+        d.s_nu = r->s_nu;
+        d.s_alpha = r->s_alpha;
+        d.nu = (1.0 / d.s_nu - 0.5) / 3.0;
+        d.alpha = CS2T * (1.0 / d.s_alpha - 0.5);
+    }
+    if (!(3.0 * d.nu + 0.5 > 0.5 + 1e-4)) return fail("tau_nu = %.6g is too close to 1/2", 3.0 * d.nu + 0.5);
+    if (!(d.s_alpha > 0.0 && d.s_alpha < 2.0)) return fail("s_alpha = %.6g outside (0, 2)", d.s_alpha);
+    d.gbeta = Ra > 0.0 ? Ra * d.nu * d.alpha / ((Th - Tm) * std::pow((double)d.H, 3)) : 0.0;
+    d.s_e = pick(r->s_e, 1.19);
+    d.s_eps = pick(r->s_eps, 1.4);
+    d.s_q = pick(r->s_q, 1.2);
+    d.s_pi = pick(r->s_pi, 1.4);
+    d.s_m = pick(r->s_m, 1.98);
+    d.s_g4 = pick(r->s_g4, 1.0);
+    d.s_g5 = pick(r->s_g5, 1.0);
+    const double rs[7] = {d.s_e, d.s_eps, d.s_q, d.s_pi, d.s_m, d.s_g4, d.s_g5};
+    for (double v : rs)
+        if (!(v < 2.0)) return fail("relaxation rates must be below 2");
+    d.s0 = g->s0 > 0.0 ? g->s0 : 1.0;
+    if (!(d.s0 >= 0.5 && d.s0 <= d.H)) return fail("s0 must be in [0.5, H]");
+    d.lambda = neumann_lambda(Ste);
+    d.t0 = Ste > 0.0 ? d.s0 * d.s0 / (4.0 * d.lambda * d.lambda * d.alpha) : 0.0;
+    return LBM_OK;
+}
+
+}  // namespace
+
+struct lbm_melt {
+    KP kp;
+    Derived d;
+    int face, precision;
+    double Ste, Th, Tc, Tm;
+    cudaStream_t stream;
+    int device;
+    void *F, *G;
+    int *js[2];
+    double *s[2];
+    int cur;
+    float *gpost;
+    float *thw_cur, *thw_prev;
+    int thw_pending;   // set_hot_wall happened while values were in flight
+    int *status_dev;
+    double *sum_dev;
+    int inflight;      // last stream-collide was an even (local) step
+    long long steps;
+    size_t bytes;
+    int timing;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs of timed launches
+    size_t ev_used;
+    char err[512];
+};
+
+namespace {
+
+lbm_status set_err(lbm_melt *h, lbm_status st, const char *fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof h->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+lbm_status cuda_err(lbm_melt *h, cudaError_t e, const char *where) {
+    return set_err(h, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", where,
+                   cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_err(h, e_, where); \
+    } while (0)
+
+Bufs bufs(lbm_melt *h) {
+    Bufs b;
+    b.F = h->F;
+    b.G = h->G;
+    b.js = h->js[h->cur];
+    b.js_next = h->js[1 - h->cur];
+    b.s = h->s[h->cur];
+    b.s_next = h->s[1 - h->cur];
+    b.gpost = h->gpost;
+    b.thw_rd = h->thw_pending ? h->thw_prev : h->thw_cur;
+    b.thw_wr = h->thw_cur;
+    b.status = h->status_dev;
+    return b;
+}
+
+#define LAUNCH(h, method, ...)                                                       \
+    ((h)->precision == 1 ? lbm::Launch<__half>::method(__VA_ARGS__)                  \
+                         : lbm::Launch<float>::method(__VA_ARGS__))
+
+// Prepare js from s and the ghost nodes from the state (front held).
+lbm_status refresh_front(lbm_melt *h) {
+    Bufs b = bufs(h);
+    CK(LAUNCH(h, front, h->kp, h->face, h->inflight, 0, b, h->stream), "front refresh");
+    h->cur ^= 1;
+    return LBM_OK;
+}
+
+lbm_status copy_in(lbm_melt *h, void *dst, const void *src, size_t bytes, int ptr_kind) {
+    CK(cudaMemcpyAsync(dst, src, bytes, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
+       "copy in");
+    return LBM_OK;
+}
+
+lbm_status check_status(lbm_melt *h) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    if (st & 2) return set_err(h, LBM_ENAN, "non-finite temperature at the front");
+    if (st & 1) return set_err(h, LBM_EUNSTABLE, "the front moved more than half a cell in one step");
+    return LBM_OK;
+}
+
+void free_all(lbm_melt *h) {
+    cudaFree(h->F);
+    cudaFree(h->G);
+    for (int k = 0; k < 2; ++k) { cudaFree(h->js[k]); cudaFree(h->s[k]); }
+    cudaFree(h->gpost);
+    cudaFree(h->thw_cur);
+    cudaFree(h->thw_prev);
+    cudaFree(h->status_dev);
+    cudaFree(h->sum_dev);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+}
+
+// Deterministic FP64 sum of n values in one block (fixed order).
+__global__ void k_sum(const double *__restrict__ v, long long n, double scale, double *__restrict__ out) {
+    __shared__ double sh[1024];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] * scale;
+}
+
+__global__ void k_fill_f(float *p, long long n, float v) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void k_fill_d(double *p, long long n, double v) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
+
+LBM_API lbm_status lbm_melt_derive(const lbm_melt_grid *grid, double Ra, double Pr, double Ste, double Th,
+                                   double Tc, double Tm, const lbm_melt_rates *rates, lbm_melt_info *info) {
+    Derived d;
+    lbm_status st = derive(grid, Ra, Pr, Ste, Th, Tc, Tm, rates, d, nullptr, 0);
+    if (st != LBM_OK || !info) return st;
+    std::memset(info, 0, sizeof *info);
+    info->nu = d.nu;
+    info->alpha = d.alpha;
+    info->gbeta = d.gbeta;
+    info->tau_nu = 3.0 * d.nu + 0.5;
+    info->s_nu = d.s_nu;
+    info->s_alpha = d.s_alpha;
+    info->lambda = d.lambda;
+    info->t0 = d.t0;
+    info->H = d.H;
+    info->n_cells = d.N;
+    info->n_columns = d.ncols;
+    return LBM_OK;
+}
+
+// Validation message of lbm_melt_derive's rejection (static buffer, not
+// thread-safe; for diagnostics).
+LBM_API const char *lbm_melt_derive_error(const lbm_melt_grid *grid, double Ra, double Pr, double Ste, double Th,
+                                          double Tc, double Tm, const lbm_melt_rates *rates) {
+    static char msg[256];
+    Derived d;
+    msg[0] = 0;
+    derive(grid, Ra, Pr, Ste, Th, Tc, Tm, rates, d, msg, sizeof msg);
+    return msg;
+}
+
+LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double Pr, double Ste, double Th,
+                                   double Tc, double Tm, const lbm_melt_rates *rates, void *cuda_stream,
+                                   lbm_melt **out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    Derived d;
+    lbm_status st = derive(grid, Ra, Pr, Ste, Th, Tc, Tm, rates, d, nullptr, 0);
+    if (st != LBM_OK) return st;
+    lbm_melt *h = new (std::nothrow) lbm_melt();
+    if (!h) return LBM_ENOMEM;
+    h->d = d;
+    h->face = grid->heated_face;
+    h->precision = grid->precision;
+    h->Ste = Ste; h->Th = Th; h->Tc = Tc; h->Tm = Tm;
+    h->stream = (cudaStream_t)cuda_stream;
+    KP &p = h->kp;
+    p.nx = grid->nx; p.ny = grid->ny; p.nz = grid->nz;
+    p.H = d.H; p.P1 = d.P1; p.P2 = d.P2; p.ncols = (int)d.ncols;
+    p.N = d.N;
+    p.ld = (d.N + 127) / 128 * 128;  // 256-byte aligned direction arrays (fp16) / 512 (fp32)
+    p.Tm = (float)Tm; p.Tc = (float)Tc; p.gbeta = (float)d.gbeta;
+    p.s_e = (float)d.s_e; p.s_eps = (float)d.s_eps; p.s_q = (float)d.s_q; p.s_nu = (float)d.s_nu;
+    p.s_pi = (float)d.s_pi; p.s_m = (float)d.s_m;
+    p.s_alpha = (float)d.s_alpha; p.s_g4 = (float)d.s_g4; p.s_g5 = (float)d.s_g5;
+    p.Tm_d = Tm; p.Th_d = Th;
+    p.coef = Ste > 0.0 ? d.alpha * Ste / (Th - Tm) : 0.0;
+    auto fail = [&](lbm_status s) { free_all(h); delete h; return s; };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(LBM_ECUDA);
+    const size_t es = h->precision == 1 ? sizeof(__half) : sizeof(float);
+    const size_t nF = 19 * (size_t)p.ld * es, nG = 7 * (size_t)p.ld * es;
+    const size_t nc = (size_t)d.ncols;
+    struct { void **p; size_t b; } allocs[] = {
+        {&h->F, nF}, {&h->G, nG}, {(void **)&h->js[0], nc * 4}, {(void **)&h->js[1], nc * 4},
+        {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
+        {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
+        {(void **)&h->sum_dev, 8}};
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.p, a.b);
+        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+        h->bytes += a.b;
+    }
+    // Initial state (reading of the paper's initial condition: a front at s0
+    // with the liquid below at the Neumann temperature of that front).
+    std::vector<float> Tprof(d.H);
+    for (int j = 0; j < d.H; ++j) {
+        const double a = j + 0.5;
+        Tprof[j] = (float)(Ste > 0.0 ? Th - (Th - Tm) * std::erf(a / (2.0 * std::sqrt(d.alpha * d.t0))) /
+                                                std::erf(d.lambda)
+                                     : Tm);
+    }
+    float *Tprof_dev = nullptr;
+    if (cudaMalloc(&Tprof_dev, sizeof(float) * d.H) != cudaSuccess) return fail(LBM_ENOMEM);
+    const int nb = (int)((nc + 255) / 256);
+    cudaError_t e = cudaMemcpyAsync(Tprof_dev, Tprof.data(), sizeof(float) * d.H, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->F, 0, nF, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->G, 0, nG, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->js[0], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gpost, 0, 7 * nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) {
+        k_fill_d<<<nb, 256, 0, h->stream>>>(h->s[0], (long long)nc, d.s0);
+        k_fill_f<<<nb, 256, 0, h->stream>>>(h->thw_cur, (long long)nc, (float)Th);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        // liquid counts of the initial front (front held), then the initial
+        // distributions, then the ghost nodes of that state
+        h->cur = 0;
+        h->inflight = 0;
+        Bufs b = bufs(h);
+        e = LAUNCH(h, front, p, h->face, 0, 0, b, h->stream);
+        if (e == cudaSuccess) {
+            h->cur = 1;
+            b = bufs(h);
+            e = LAUNCH(h, init, p, h->face, b, Tprof_dev, h->stream);
+        }
+    }
+    if (e == cudaSuccess && refresh_front(h) != LBM_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(Tprof_dev);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    *out = h;
+    return LBM_OK;
+}
+
+LBM_API void lbm_melt_destroy(lbm_melt *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+LBM_API const char *lbm_melt_last_error(const lbm_melt *h) { return h ? h->err : "null handle"; }
+
+LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
+    if (!h) return LBM_EINVAL;
+    if (n < 0) return set_err(h, LBM_EINVAL, "negative step count");
+    const dim3 blk = lbm::node_block(h->kp);
+    for (long long t = 0; t < n; ++t) {
+        Bufs b = bufs(h);
+        const int odd = h->inflight;
+        cudaEvent_t *evp = nullptr;
+        if (h->timing) {
+            if (h->ev_used + 2 > h->ev.size()) {
+                for (int k = 0; k < 64; ++k) {
+                    cudaEvent_t ev;
+                    CK(cudaEventCreate(&ev), "event create");
+                    h->ev.push_back(ev);
+                }
+            }
+            evp = &h->ev[h->ev_used];
+            h->ev_used += 2;
+            CK(cudaEventRecord(evp[0], h->stream), "event record");
+        }
+        CK(LAUNCH(h, stream_collide, h->kp, h->face, odd, b, blk, h->stream), "stream-collide");
+        if (evp) CK(cudaEventRecord(evp[1], h->stream), "event record");
+        h->inflight = !odd;
+        if (odd) h->thw_pending = 0;
+        b = bufs(h);
+        CK(LAUNCH(h, front, h->kp, h->face, h->inflight, 1, b, h->stream), "front");
+        CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, b, h->stream), "flip");
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_sync(lbm_melt *h) {
+    if (!h) return LBM_EINVAL;
+    return check_status(h);
+}
+
+LBM_API lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction, int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    const KP &p = h->kp;
+    const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
+    float *Td = nullptr, *ud = nullptr;
+    if (T || u) {
+        if (ptr_kind) { Td = T; ud = u; }
+        else {
+            if (T) CK(cudaMalloc(&Td, N * 4), "alloc T");
+            if (u) CK(cudaMalloc(&ud, 3 * N * 4), "alloc u");
+        }
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, macro, p, h->face, h->inflight, b, Td, ud, h->stream), "macro");
+        if (!ptr_kind) {
+            if (T) CK(cudaMemcpyAsync(T, Td, N * 4, cudaMemcpyDeviceToHost, h->stream), "copy T");
+            if (u) CK(cudaMemcpyAsync(u, ud, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream), "copy u");
+        }
+    }
+    if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream), "copy S");
+    if (liquid_fraction) {
+        k_sum<<<1, 1024, 0, h->stream>>>(h->s[h->cur], (long long)nc, 1.0 / ((double)p.H * (double)nc), h->sum_dev);
+        CK(cudaGetLastError(), "sum");
+        CK(cudaMemcpyAsync(liquid_fraction, h->sum_dev, 8,
+                           ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream), "copy lf");
+    }
+    lbm_status st = check_status(h);
+    if (!ptr_kind) { cudaFree(Td); cudaFree(ud); }
+    return st;
+}
+
+LBM_API lbm_status lbm_melt_get_state(lbm_melt *h, float *f, float *g, double *S, int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    const KP &p = h->kp;
+    const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
+    float *fd = nullptr, *gd = nullptr;
+    if (f || g) {
+        if (ptr_kind) { fd = f; gd = g; }
+        else {
+            if (f) CK(cudaMalloc(&fd, 19 * N * 4), "alloc f");
+            if (g) CK(cudaMalloc(&gd, 7 * N * 4), "alloc g");
+        }
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, state_out, p, h->face, h->inflight, b, fd, gd, h->stream), "state out");
+        if (!ptr_kind) {
+            if (f) CK(cudaMemcpyAsync(f, fd, 19 * N * 4, cudaMemcpyDeviceToHost, h->stream), "copy f");
+            if (g) CK(cudaMemcpyAsync(g, gd, 7 * N * 4, cudaMemcpyDeviceToHost, h->stream), "copy g");
+        }
+    }
+    if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream), "copy S");
+    lbm_status st = check_status(h);
+    if (!ptr_kind) { cudaFree(fd); cudaFree(gd); }
+    return st;
+}
+
+LBM_API lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *g, const double *S, int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    if (S && (!f || !g)) return set_err(h, LBM_EINVAL, "a new front needs f and g too");
+    const KP &p = h->kp;
+    const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
+    // Bring the layout to natural first, so that kept parts stay valid.
+    if (h->inflight && (!f || !g)) {
+        float *fd = nullptr, *gd = nullptr;
+        CK(cudaMalloc(&fd, 19 * N * 4), "alloc f");
+        CK(cudaMalloc(&gd, 7 * N * 4), "alloc g");
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, state_out, p, h->face, 1, b, fd, gd, h->stream), "state out");
+        CK(LAUNCH(h, state_in, p, h->face, b, fd, gd, h->stream), "state in");
+        CK(cudaStreamSynchronize(h->stream), "synchronize");
+        cudaFree(fd);
+        cudaFree(gd);
+    }
+    h->inflight = 0;
+    h->thw_pending = 0;
+    if (S) {
+        lbm_status st = copy_in(h, h->s[h->cur], S, nc * 8, ptr_kind);
+        if (st != LBM_OK) return st;
+        // liquid counts from the new fronts, front held
+        if ((st = refresh_front(h)) != LBM_OK) return st;
+    }
+    const float *fd = f, *gd = g;
+    float *tf = nullptr, *tg = nullptr;
+    if (!ptr_kind) {
+        if (f) { CK(cudaMalloc(&tf, 19 * N * 4), "alloc f"); CK(cudaMemcpyAsync(tf, f, 19 * N * 4, cudaMemcpyHostToDevice, h->stream), "copy f"); fd = tf; }
+        if (g) { CK(cudaMalloc(&tg, 7 * N * 4), "alloc g"); CK(cudaMemcpyAsync(tg, g, 7 * N * 4, cudaMemcpyHostToDevice, h->stream), "copy g"); gd = tg; }
+    }
+    if (f || g) {
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, state_in, p, h->face, b, fd, gd, h->stream), "state in");
+    }
+    lbm_status st = refresh_front(h);
+    if (st == LBM_OK) st = check_status(h);
+    cudaFree(tf);
+    cudaFree(tg);
+    return st;
+}
+
+LBM_API lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, int ptr_kind) {
+    if (!h || !T_h_field) return LBM_EINVAL;
+    const size_t nc = (size_t)h->kp.ncols;
+    if (h->inflight && !h->thw_pending) {
+        // the pending odd step must still read the walls with the field of
+        // the step that produced the in-flight values
+        CK(cudaMemcpyAsync(h->thw_prev, h->thw_cur, nc * 4, cudaMemcpyDeviceToDevice, h->stream), "copy wall");
+        h->thw_pending = 1;
+    }
+    return copy_in(h, h->thw_cur, T_h_field, nc * 4, ptr_kind);
+}
+
+LBM_API lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info) {
+    if (!h || !info) return LBM_EINVAL;
+    std::memset(info, 0, sizeof *info);
+    const Derived &d = h->d;
+    info->nu = d.nu;
+    info->alpha = d.alpha;
+    info->gbeta = d.gbeta;
+    info->tau_nu = 3.0 * d.nu + 0.5;
+    info->s_nu = d.s_nu;
+    info->s_alpha = d.s_alpha;
+    info->lambda = d.lambda;
+    info->t0 = d.t0;
+    info->H = d.H;
+    info->n_cells = d.N;
+    info->n_columns = d.ncols;
+    info->steps = h->steps;
+    info->device_bytes = h->bytes;
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_set_timing(lbm_melt *h, int enable) {
+    if (!h) return LBM_EINVAL;
+    h->timing = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, int reset) {
+    if (!h) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, h->ev[k], h->ev[k + 1]), "event elapsed");
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = (long long)(h->ev_used / 2);
+    if (reset) h->ev_used = 0;
+    return LBM_OK;
+}

@@ -1,0 +1,174 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Tolerances: max |dT| <= 1e-4 and |d liquid
+fraction| <= 1e-3 for FP32 storage; distributions after a few steps from a
+given state within 2e-6 (FP32 rounding of O(1e-2) shifted values)."""
+import numpy as np
+import pytest
+
+from paper_1604_03478_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+W7 = np.array([1 / 4] + [1 / 8] * 6)
+TOL_T, TOL_LF = 1e-4, 1e-3
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1604_03478_gb300 import build, Cavity
+    build.build()
+    return Cavity
+
+
+def _pair(lib, orc, shape, **kw):
+    return lib(*shape, **kw), orc.Oracle(*shape, **kw)
+
+
+def _compare(gpu, o, tol_T=TOL_T, tol_lf=TOL_LF, tol_u=1e-4):
+    Tg, ug, Sg, lfg = gpu.get()
+    To, uo, So, lfo = o.get()
+    dT = np.abs(Tg - To).max()
+    du = np.abs(ug - uo).max()
+    dS = np.abs(Sg - So).max()
+    assert dT <= tol_T, ("T", dT)
+    assert abs(lfg - lfo) <= tol_lf, ("lf", lfg, lfo)
+    assert du <= tol_u, ("u", du)
+    assert dS <= tol_lf, ("S", dS)
+    return dT, du, dS, abs(lfg - lfo)
+
+
+def test_conduction_32cube_1000_steps(lib, orc):
+    """Plain method, conduction-controlled melting in a 32^3 cube, Ra = 0,
+    Ste = 0.1, alpha = 0.25, 1000 steps."""
+    kw = dict(face=0, Ra=0.0, Ste=0.1, s_nu=1 / 0.8, s_alpha=2 / 3)
+    gpu, o = _pair(lib, orc, (32, 32, 32), **kw)
+    gpu.step(1000)
+    o.step(1000)
+    _compare(gpu, o, tol_u=1e-6)
+
+
+@pytest.mark.parametrize("face,shape", [(0, (40, 24, 20)), (1, (36, 20, 26))])
+@pytest.mark.parametrize("steps", [150, 151])
+def test_convection_melting(lib, orc, face, shape, steps):
+    """Ra > 0, both heated faces, odd and even step counts (both AA phases),
+    a ragged x extent (not a multiple of 32)."""
+    kw = dict(face=face, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
+    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu.step(steps)
+    o.step(steps)
+    _compare(gpu, o)
+
+
+def _random_state(o, seed, s_lo, s_hi, amp=2e-3):
+    nz, ny, nx = o.shape
+    H = o.H
+    s = inputs.uniform(o.ncols, s_lo, s_hi, seed)
+    a = (np.arange(ny) if o.face == 0 else np.arange(nz)) + 0.5
+    # column index and axial coordinate per node
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    col = (Z * nx + X) if o.face == 0 else (Y * nx + X)
+    ax = (Y if o.face == 0 else Z) + 0.5
+    sc = s[col]
+    liq = (ax < sc).reshape(-1)
+    T = np.where(ax < sc, 1.0 - ax / sc, 0.0).reshape(-1)
+    f = inputs.noisy(np.tile(W19[:, None], (1, o.N)), amp, seed + 1)
+    f[:, ~liq] = 0.0
+    g = inputs.noisy(W7[:, None] * T[None, :], amp, seed + 2)
+    return f.astype(np.float32), g.astype(np.float32), s
+
+
+@pytest.mark.parametrize("face", [0, 1])
+@pytest.mark.parametrize("nsteps", [1, 2, 3])
+def test_steps_from_random_state(lib, orc, face, nsteps):
+    """A non-flat front and perturbed populations: after 1, 2, 3 steps the
+    distributions of every node agree (liquid f, all g)."""
+    shape = (13, 10, 9) if face == 0 else (13, 9, 10)
+    kw = dict(face=face, Ra=2e4, Pr=0.5, Ste=0.3, Ma=0.15, derive=True)
+    gpu, o = _pair(lib, orc, shape, **kw)
+    f, g, s = _random_state(o, 7 + face, 2.2, 7.8)
+    o.set_state(f.astype(np.float64), g.astype(np.float64), s)
+    gpu.set_state(f, g, s)
+    gpu.step(nsteps)
+    o.step(nsteps)
+    fg, gg, sg = gpu.get_state()
+    fo, go, so = o.get_state()
+    np.testing.assert_allclose(sg, so, atol=1e-7, rtol=0)
+    np.testing.assert_allclose(gg, go, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(fg, fo, atol=2e-6, rtol=0)
+
+
+@pytest.mark.parametrize("face", [0, 1])
+def test_flips_after_even_and_odd_steps(lib, orc, face):
+    """Fronts placed just below node centres so that nodes melt in the first
+    (even, values in flight) and second (odd) steps: the link rewrite of the
+    flip must reproduce the oracle's double-buffered streaming."""
+    shape = (12, 10, 11) if face == 0 else (12, 11, 10)
+    kw = dict(face=face, Ra=0.0, Ste=1.0, s_nu=1.3, s_alpha=1.5)
+    gpu, o = _pair(lib, orc, shape, **kw)
+    f, g, s = _random_state(o, 21 + face, 2.0, 6.0)
+    # put every front 0.01..0.03 below a node centre
+    s = np.floor(s) + 0.5 - inputs.uniform(s.shape, 0.01, 0.03, 5)
+    o.set_state(f.astype(np.float64), g.astype(np.float64), s)
+    gpu.set_state(f, g, s)
+    js0 = np.ceil(s - 0.5)
+    for n in range(1, 5):
+        gpu.step(1)
+        o.step(1)
+        fg, gg, sg = gpu.get_state()
+        fo, go, so = o.get_state()
+        np.testing.assert_allclose(sg, so, atol=1e-7, rtol=0)
+        np.testing.assert_allclose(fg, fo, atol=2e-6, rtol=0)
+        np.testing.assert_allclose(gg, go, atol=2e-6, rtol=0)
+        if n == 1:
+            assert (np.ceil(so - 0.5) > js0).mean() > 0.5  # most columns flipped in the even step
+
+
+def test_state_roundtrip(lib, orc):
+    gpu = lib(11, 12, 9, face=0, Ra=0.0, Ste=0.5, s_nu=1.2, s_alpha=1.0)
+    o = orc.Oracle(11, 12, 9, face=0, Ra=0.0, Ste=0.5, s_nu=1.2, s_alpha=1.0)
+    f, g, s = _random_state(o, 3, 2.0, 9.0)
+    gpu.set_state(f, g, s)
+    f2, g2, s2 = gpu.get_state()
+    np.testing.assert_array_equal(s2, s)
+    np.testing.assert_allclose(g2, g, atol=1e-7)
+    np.testing.assert_allclose(f2, f, atol=1e-7)
+    gpu.step(1)  # values now in flight
+    f3, g3, s3 = gpu.get_state()
+    gpu.set_state(f3, g3, s3)
+    f4, g4, s4 = gpu.get_state()
+    np.testing.assert_allclose(f4, f3, atol=1e-7)
+    np.testing.assert_allclose(g4, g3, atol=1e-7)
+
+
+@pytest.mark.parametrize("when", [0, 1])
+def test_hot_wall_field(lib, orc, when):
+    """A seeded Gaussian perturbation of the heated-wall temperature, applied
+    after an even (values in flight) or an odd step."""
+    kw = dict(face=0, Ra=5e4, Pr=0.2, Ste=0.5, Ma=0.15, s0=2.5, derive=True)
+    gpu, o = _pair(lib, orc, (16, 14, 12), **kw)
+    gpu.step(11 + when)
+    o.step(11 + when)
+    Thw = 1.0 + inputs.gaussian_field(o.ncols, 0.05, 99)
+    gpu.set_hot_wall(Thw.astype(np.float32))
+    o.set_hot_wall(Thw.astype(np.float32).astype(np.float64))
+    gpu.step(40)
+    o.step(40)
+    _compare(gpu, o)
+
+
+def test_fp16_storage_error(lib, orc):
+    """Shifted-FP16 storage, FP32 arithmetic: the error against the FP64
+    oracle is reported, and bounded well below the flow's own scales."""
+    kw = dict(face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
+    gpu = lib(24, 20, 16, precision=1, **kw)
+    o = orc.Oracle(24, 20, 16, **kw)
+    gpu.step(200)
+    o.step(200)
+    Tg, ug, Sg, lfg = gpu.get()
+    To, uo, So, lfo = o.get()
+    dT, dlf = np.abs(Tg - To).max(), abs(lfg - lfo)
+    print("fp16 storage: max|dT| = %.3g, |dlf| = %.3g" % (dT, dlf))
+    assert dT < 2e-2 and dlf < 2e-3
