@@ -1,0 +1,325 @@
+"""Benchmark of the double-MRT melting step on GB300.
+
+Workload (the precision-study configuration, side-heated variant): a 256^3
+cavity heated at y = 0, Ra = 1e6, Pr = 0.02, Ste = 0.05, Ma = 0.1, FP32
+storage, the front started flat at s0 = 0.4 H so that the liquid fraction is
+mid-cavity while timing.  One step = the whole hot path: the fused
+stream-collide (D3Q19 + D3Q7 MRT, AA pattern), the FP64 front update (Eq. 6)
+and the phase flip.
+
+Prints ONE JSON line.  ``value`` is liquid-node updates per second (MLUPS,
+the fluid-node convention) with the state resident in HBM; ``e2e`` is the
+same metric through the C ABI with host buffers, every step uploading the
+heated-wall field from pinned host memory and reading the front and the
+liquid fraction back.  ``--impl reference`` times the CPU FP64 oracle on the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "double-MRT melting MLUPS & % HBM roofline at 256³; adjoint/forward time ratio"
+N_EDGE = 256
+CASE = dict(face=0, Ra=1e6, Pr=0.02, Ste=0.05, Ma=0.1, s0=0.4 * N_EDGE, derive=True)
+WORKLOAD = ("256^3 cavity heated at y=0, Ra 1e6, Pr 0.02, Ste 0.05, Ma 0.1, FP32 storage, "
+            "front started flat at s0 = 0.4 H")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edge", type=int, default=N_EDGE,
+                    help="cavity edge (256 is the benchmark workload; smaller edges for profiling captures)")
+    ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d and d[k]:
+                v = d[k]
+                if isinstance(v, dict):
+                    v = v.get("value") or v.get("gbs")
+                return float(v), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, TypeError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def liquid_counts(S, H):
+    """Liquid nodes and the solid nodes the stream-collide still updates
+    (solid nodes below the 3x3-neighbourhood maximum first-solid index + 2;
+    deeper ones are provably unchanged and skipped)."""
+    js = np.clip(np.ceil(S - 0.5), 0, H).astype(np.int64)
+    pad = np.pad(js, 1, mode="edge")
+    mx = np.max(np.stack([pad[1 + di:1 + di + js.shape[0], 1 + dj:1 + dj + js.shape[1]]
+                          for di in (-1, 0, 1) for dj in (-1, 0, 1)]), axis=0)
+    n_liq = int(js.sum())
+    n_solid_active = int(np.minimum(mx + 2, H).sum() - n_liq)
+    return n_liq, max(n_solid_active, 0)
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample(steps, warm=0, n=N_EDGE):
+    """Time the FP64 oracle on the workload (edge n, same parameters, front
+    at 0.4 n) on this host's cores."""
+    import oracle
+    oracle.build()
+    case = dict(CASE, s0=0.4 * n)
+    o = oracle.Oracle(n, n, n, **case)
+    if warm:
+        o.step(warm)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n_liq = o.info()["n_liquid"]  # after the steps; the front moves < 1 cell
+    o.close()
+    return n_liq * steps / dt / 1e6, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    # each step is one oracle step of a downscaled twin of the workload, its
+    # edge chosen so that the whole run stays near 90 s of host time
+    import oracle
+    oracle.build()
+    threads = oracle.num_threads()
+    per_step = 90.0 / max(1, args.steps + args.warmup)
+    n = int((per_step * threads / 1.5e-6) ** (1.0 / 3.0)) // 16 * 16
+    n = max(32, min(N_EDGE, n))
+    value, dt, cores = oracle_sample(args.steps, warm=args.warmup, n=n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "implementation": "CPU FP64 oracle (OpenMP)",
+                                           "sample_edge": n},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d oracle steps (after %d warm-up steps) of a %d^3 twin of the workload "
+                                   "(same Ra, Pr, Ste, Ma, front at 0.4 H)" % (args.steps, args.warmup, n)},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    n = args.edge
+    cav = Cavity(n, n, n, stream=stream.cuda_stream, precision=args.precision, **dict(CASE, s0=0.4 * n))
+    H = cav.H
+    warm = max(3, args.warmup)
+    cav.step(warm)
+    cav.sync()
+    S0 = cav.get(T=False, u=False)[2]
+    n_liq0, n_sol0 = liquid_counts(S0, H)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    gpu_id = torch.cuda.get_device_properties(local).uuid
+    gpu_id = "GPU-" + str(gpu_id) if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    cav.set_timing(True)
+    cav.kernel_time(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(gpu_id) as clk:
+        ev0.record(stream)
+        cav.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    k1_ms, k1_n = cav.kernel_time(reset=True)
+    cav.set_timing(False)
+    S1 = cav.get(T=False, u=False)[2]
+    n_liq1, n_sol1 = liquid_counts(S1, H)
+    n_liq = 0.5 * (n_liq0 + n_liq1)
+    n_sol = 0.5 * (n_sol0 + n_sol1)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * n_liq * args.steps / (ms_max * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (the fused stream-collide)
+    k1_avg_ms = k1_ms / max(k1_n, 1)
+    bl, bs = (208.0, 28.0) if args.precision == 0 else (104.0, 14.0)
+    alg_bytes = bl * n_liq + bs * n_sol
+    achieved = alg_bytes / (k1_avg_ms * 1e-3) / 1e9
+    peak, peak_src = hbm_peak()
+
+    # end to end through the C ABI with host buffers
+    ncols = cav.ncols
+    thw_host = torch.full((ncols,), 1.0, dtype=torch.float32).pin_memory()
+    S_host = torch.empty((ncols,), dtype=torch.float64).pin_memory()
+    lf_host = torch.empty((1,), dtype=torch.float64).pin_memory()
+    from paper_1604_03478_gb300 import _abi
+    import ctypes as C
+    L = _abi.load()
+    h = cav._h
+    e2e_steps = args.e2e_steps
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st = L.lbm_melt_set_hot_wall(h, C.c_void_p(thw_host.data_ptr()), 0)
+        st |= L.lbm_melt_step(h, 1)
+        st |= L.lbm_melt_get(h, None, None, C.c_void_p(S_host.data_ptr()), C.c_void_p(lf_host.data_ptr()), 0)
+        if st != 0:
+            raise RuntimeError(L.lbm_melt_last_error(h).decode())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * n_liq1 * e2e_steps / e2e_s / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = oracle_sample(2, n=n)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "2 oracle steps of the full %d^3 workload from its initial state (%.1f s)" % (n, dt)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": warm, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if (n == N_EDGE and args.precision == 0) else
+                   "%d^3 cavity, %s storage, otherwise as the 256^3 workload" % (n, "FP32" if args.precision == 0
+                                                                                   else "shifted FP16"),
+                   "nodes": n ** 3, "liquid_nodes": n_liq,
+                   "liquid_fraction": float(np.mean(S1) / H), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "state 1.7 GB > L2 (inputs larger than L2, no flush)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "fused stream-collide (k_even/k_odd)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k1_avg_ms, "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": ncols * 4,
+                "d2h_bytes_per_step": ncols * 8 + 8, "steps": e2e_steps},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "all_node_mlups": world * (n ** 3) * args.steps / (ms_max * 1e-3) / 1e6,
+    }
+    cav.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

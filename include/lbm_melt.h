@@ -131,11 +131,14 @@ lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, double *liqu
 
 /* Distributions in natural form (post-streaming, pre-collision; f_i and g_i,
    not shifted), direction-major: f[i*N + node], g[i*N + node]; solid nodes
-   report f = 0.  Any pointer may be NULL.  Synchronises. */
+   report f = 0, and solid nodes whose neighbourhood is all solid report g at
+   rest at Tm.  Any pointer may be NULL.  Synchronises. */
 lbm_status lbm_melt_get_state(lbm_melt *h, float *f, float *g, double *S, int ptr_kind);
 
 /* Replace the state with natural-form distributions and front heights (same
-   layout as lbm_melt_get_state; f of solid nodes is ignored).  f or g may be
+   layout as lbm_melt_get_state).  Solid nodes are stored at rest (f and g of
+   solid nodes are ignored: a solid node's own populations never enter the
+   method, its post-collision values being reset every step).  f or g may be
    NULL to keep that part; a new S needs both f and g.  The phase flags and
    the ghost nodes are recomputed from the new state. */
 lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *g, const double *S,

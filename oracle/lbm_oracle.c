@@ -753,16 +753,21 @@ void orc_get_state(const orc_sim *S, double *f, double *g, double *s) {
     if (s) memcpy(s, S->s, sizeof(double) * S->ncols);
 }
 
-/* Replace the state; flags and ghost temperatures are recomputed from s and g. */
+/* Replace the state; flags and ghost nodes are recomputed from s and g.  A
+   solid node's own populations never enter the method (its post-collision
+   values are reset every step), so solid nodes are stored at rest: f = 0,
+   g = g^eq(Tm, 0). */
 void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s) {
     if (s) memcpy(S->s, s, sizeof(double) * S->ncols);
+    refresh_flags(S);
+    double zero[3] = {0.0, 0.0, 0.0}, gm[Q7];
+    geq7(S->cfg.Tm, zero, gm);
     if (f)
         for (long c = 0; c < S->N; ++c)
-            for (int i = 0; i < Q19; ++i) S->f[c * Q19 + i] = f[(long)i * S->N + c];
+            for (int i = 0; i < Q19; ++i) S->f[c * Q19 + i] = S->liq[c] ? f[(long)i * S->N + c] : 0.0;
     if (g)
         for (long c = 0; c < S->N; ++c)
-            for (int i = 0; i < Q7; ++i) S->g[c * Q7 + i] = g[(long)i * S->N + c];
-    refresh_flags(S);
+            for (int i = 0; i < Q7; ++i) S->g[c * Q7 + i] = S->liq[c] ? g[(long)i * S->N + c] : gm[i];
     refresh_ghosts(S);
 }
 

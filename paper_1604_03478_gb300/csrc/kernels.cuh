@@ -44,10 +44,21 @@ __device__ __forceinline__ void solid_post(const KP &p, bool ghost, const float 
     for (int i = 0; i < 7; ++i) g[i] = ghost ? __ldg(gpost + (long long)i * p.ncols + col) : 0.0f;
 }
 
+// A solid node at least two nodes above its column's first solid node and
+// above every 3x3-neighbour column's first solid node ("deep") has only
+// solid neighbours that are not ghost nodes.  Nothing reads its slots while
+// it is deep, and one step before the front can reach it, it is no longer
+// deep (the 3x3 maximum includes its own column), so with Tc = Tm (the cold
+// wall then returns zero too) its update can be skipped exactly.
+__device__ __forceinline__ bool deep_solid(const KP &p, int a, int nbv) {
+    return p.skip_deep && a >= (nbv & 0xffff) + 2;
+}
+
 // ------------------------------------------------------------- even step
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__restrict__ G,
-                                              const int *__restrict__ js, const float *__restrict__ gpost) {
+                                              const int *__restrict__ js, const int *__restrict__ nb,
+                                              const float *__restrict__ gpost) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -67,6 +78,7 @@ __global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__re
 #pragma unroll
         for (int i = 0; i < 19; ++i) Store<ST>::st(F + opp(i) * p.ld + c, f[i]);
     } else {
+        if (deep_solid(p, a, __ldg(nb + col))) return;
         solid_post(p, a == jsc, gpost, col, g);
     }
 #pragma unroll
@@ -74,10 +86,40 @@ __global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__re
 }
 
 // -------------------------------------------------------------- odd step
+// Bit i (1..18) of the link mask: node x - e_i is inside and liquid, i.e.
+// f_i streams in from there (else halfway bounce-back).  Since x + e_i =
+// x - e_opp(i), bit opp(i) tells whether f*_i streams out to x + e_i.
+template <int FACE>
+__device__ __forceinline__ unsigned link_mask(const KP &p, const int *js, int x, int y, int z) {
+    unsigned m = 0;
+#pragma unroll
+    for (int i = 1; i < 19; ++i)
+        if (liquid_at<FACE>(p, js, x - ex(i), y - ey(i), z - ez(i))) m |= 1u << i;
+    return m;
+}
+// Bit i (1..6): node x - t_i is inside (else the link crosses a wall).
+__device__ __forceinline__ unsigned inside_mask(const KP &p, int x, int y, int z) {
+    unsigned m = 0;
+#pragma unroll
+    for (int i = 1; i < 7; ++i)
+        if (inside(p, x - tx(i), y - ty(i), z - tz(i))) m |= 1u << i;
+    return m;
+}
+
+// Wall rule for a D3Q7 population leaving along link direction `dir`
+// across a wall: adiabatic bounce-back keeps it, the isothermal walls return
+// -v + 2 w (Tw - Tm) (anti-bounce-back, shifted populations).
+template <int FACE>
+__device__ __forceinline__ float wall_value(const KP &p, int dir, float v, float Th_col) {
+    const int w = wall_of_link<FACE>(dir);
+    return w == 3 ? v : -v + 2.0f * w7(dir) * ((w == 1 ? Th_col : p.Tc) - p.Tm);
+}
+
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__restrict__ G,
-                                             const int *__restrict__ js, const float *__restrict__ gpost,
-                                             const float *__restrict__ thw_rd, const float *__restrict__ thw_wr) {
+                                             const int *__restrict__ js, const int *__restrict__ nb,
+                                             const float *__restrict__ gpost, const float *__restrict__ thw_rd,
+                                             const float *__restrict__ thw_wr) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -86,52 +128,62 @@ __global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__res
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
     const int jsc = __ldg(js + col);
+    const int nbv = __ldg(nb + col);
+    const int q = FACE == 0 ? z : y, nq = FACE == 0 ? p.nz : p.ny;
+    const bool off_walls = x >= 1 && x <= p.nx - 2 && q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
+    ST *const Fc = F + c;
+    ST *const Gc = G + c;
     float g[7];
     if (a < jsc) {
+        // interior: off the walls and at least one node below the lowest
+        // first-solid node of the 3x3 neighbour columns: every link streams
+        const bool interior = off_walls && a + 1 < (nbv >> 16);
         float f[19];
-        f[0] = Store<ST>::ld(F + c);
+        unsigned lm = 0x7fffeu, im = 0x7eu;
+        if (interior) {
 #pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            if (liquid_at<FACE>(p, js, x - ex(i), y - ey(i), z - ez(i)))
-                f[i] = Store<ST>::ld(F + opp(i) * p.ld + (c - off19<FACE>(p, i)));
-            else  // halfway bounce-back: f*_opp(i) of this node, parked in slot i
-                f[i] = Store<ST>::ld(F + i * p.ld + c);
-        }
-        g[0] = Store<ST>::ld(G + c);
+            for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(Fc + p.fin[i]);
 #pragma unroll
-        for (int i = 1; i < 7; ++i) {
-            if (inside(p, x - tx(i), y - ty(i), z - tz(i))) {
-                g[i] = Store<ST>::ld(G + opp7(i) * p.ld + (c - off7<FACE>(p, i)));
-            } else {
-                const int w = wall_of_link<FACE>(opp7(i));
-                const float own = Store<ST>::ld(G + i * p.ld + c);
-                if (w == 3) g[i] = own;  // adiabatic: bounce-back
-                else g[i] = -own + 2.0f * w7(i) * ((w == 1 ? __ldg(thw_rd + col) : p.Tc) - p.Tm);
+            for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(Gc + p.gin[i]);
+        } else {
+            lm = link_mask<FACE>(p, js, x, y, z);
+            im = inside_mask(p, x, y, z);
+            const float th_rd = __ldg(thw_rd + col);
+            f[0] = Store<ST>::ld(Fc);
+#pragma unroll
+            for (int i = 1; i < 19; ++i)  // else bounce-back: f*_opp(i) parked in slot i
+                f[i] = Store<ST>::ld(((lm >> i) & 1u) ? Fc + p.fin[i] : Fc + i * p.ld);
+            g[0] = Store<ST>::ld(Gc);
+#pragma unroll
+            for (int i = 1; i < 7; ++i) {
+                const bool in = (im >> i) & 1u;
+                const float v = Store<ST>::ld(in ? Gc + p.gin[i] : Gc + i * p.ld);
+                g[i] = in ? v : wall_value<FACE>(p, opp7(i), v, th_rd);
             }
         }
         collide(p, f, g);
+        if (interior) {
 #pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            if (liquid_at<FACE>(p, js, x + ex(i), y + ey(i), z + ez(i)))
-                Store<ST>::st(F + i * p.ld + (c + off19<FACE>(p, i)), f[i]);
-            else
-                Store<ST>::st(F + opp(i) * p.ld + c, f[i]);
+            for (int i = 0; i < 19; ++i) Store<ST>::st(Fc + p.fout[i], f[i]);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) Store<ST>::st(Gc + p.gout[i], g[i]);
+            return;
         }
-        Store<ST>::st(F + c, f[0]);
+        Store<ST>::st(Fc, f[0]);
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            Store<ST>::st(((lm >> opp(i)) & 1u) ? Fc + p.fout[i] : Fc + opp(i) * p.ld, f[i]);
     } else {
+        if (deep_solid(p, a, nbv)) return;
         solid_post(p, a == jsc, gpost, col, g);
     }
-    Store<ST>::st(G + c, g[0]);
+    const unsigned im = off_walls ? 0x7eu : inside_mask(p, x, y, z);
+    const float th_wr = __ldg(thw_wr + col);
+    Store<ST>::st(Gc, g[0]);
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
-        if (inside(p, x + tx(i), y + ty(i), z + tz(i))) {
-            Store<ST>::st(G + i * p.ld + (c + off7<FACE>(p, i)), g[i]);
-        } else {
-            const int w = wall_of_link<FACE>(i);
-            if (w == 3) Store<ST>::st(G + opp7(i) * p.ld + c, g[i]);
-            else Store<ST>::st(G + opp7(i) * p.ld + c,
-                               -g[i] + 2.0f * w7(i) * ((w == 1 ? __ldg(thw_wr + col) : p.Tc) - p.Tm));
-        }
+        const bool out = (im >> opp7(i)) & 1u;
+        Store<ST>::st(out ? Gc + p.gout[i] : Gc + opp7(i) * p.ld, out ? g[i] : wall_value<FACE>(p, i, g[i], th_wr));
     }
 }
 
@@ -224,12 +276,15 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
         if (k < 0) {
             Gr = (Tm - Tw) / sc;
         } else {
-            const double x1 = k + 0.5, y1 = node_T<ST, FACE>(p, G, col, k, infl, thw), x2 = sc, y2 = Tm;
-            double x0, y0;
-            if (k >= 1) { x0 = k - 0.5; y0 = node_T<ST, FACE>(p, G, col, k - 1, infl, thw); }
-            else        { x0 = 0.0; y0 = Tw; }
-            Gr = y0 * (x2 - x1) / ((x0 - x1) * (x0 - x2)) + y1 * (x2 - x0) / ((x1 - x0) * (x1 - x2))
-               + y2 * (2.0 * x2 - x0 - x1) / ((x2 - x0) * (x2 - x1));
+            // derivative at x2 = s of the quadratic through (x0, y0), (x1, y1),
+            // (x2, Tm): with h = x1 - x0, d1 = x2 - x1, d0 = x2 - x0,
+            // p'(x2) = (y0 d1^2 - y1 d0^2 + Tm h (d0 + d1)) / (h d0 d1)
+            const double y1 = node_T<ST, FACE>(p, G, col, k, infl, thw);
+            const double x1 = k + 0.5;
+            const double x0 = k >= 1 ? k - 0.5 : 0.0;
+            const double y0 = k >= 1 ? node_T<ST, FACE>(p, G, col, k - 1, infl, thw) : Tw;
+            const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
+            Gr = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
         }
         const double v = p.coef * (1.0 + sp * sp + sq * sq) * (-Gr);
         if (!isfinite(Gr)) atomicOr(status, 2);
@@ -248,9 +303,13 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
     double Tg;
     if (kg < 0) Tg = Tm + (Tm - Tw) * (yg - sn) / sn;
     else Tg = Tm + (Tm - node_T<ST, FACE>(p, G, col, kg, infl, thw)) * (yg - sn) / (sn - (kg + 0.5));
-    double gh[7];
+    // ghost populations (FP32, like the collision): rest equilibrium at the
+    // ghost temperature plus the non-equilibrium part N^-1 (I - Q)(n - n^eq)
+    // of the post-collision populations of the liquid node below
+    float gh[7];
+    const float dTg = (float)(Tg - Tm);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gh[i] = (double)w7(i) * (Tg - Tm);
+    for (int i = 0; i < 7; ++i) gh[i] = w7(i) * dTg;
     if (jn >= 1) {
         int x, y, z;
         column_node<FACE>(p, col, jn - 1, x, y, z);
@@ -263,33 +322,32 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
         } else {
             gather_f<ST, FACE>(p, F, js, x, y, z, infl, fL);
         }
-        double Th = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+        float Th = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 7; ++i) Th += (double)gL[i];
+        for (int i = 0; i < 7; ++i) Th += gL[i];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            jx += ex(i) * (double)fL[i];
-            jy += ey(i) * (double)fL[i];
-            jz += ez(i) * (double)fL[i];
+            jx += ex(i) * fL[i];
+            jy += ey(i) * fL[i];
+            jz += ez(i) * fL[i];
         }
-        const double TL = Th + Tm;
-        const double ux = jx, uy = jy, uz = jz + 0.5 * (double)p.gbeta * Th;
-        double dn[7];
-        dn[0] = 0.0;
-        dn[1] = ((double)gL[1] - gL[2] - ux * TL) * (1.0 - p.s_alpha) / nnorm(1);
-        dn[2] = ((double)gL[3] - gL[4] - uy * TL) * (1.0 - p.s_alpha) / nnorm(2);
-        dn[3] = ((double)gL[5] - gL[6] - uz * TL) * (1.0 - p.s_alpha) / nnorm(3);
-        dn[4] = (6.0 * gL[0] - ((double)gL[1] + gL[2] + gL[3] + gL[4] + gL[5] + gL[6]) - 0.75 * Th)
-              * (1.0 - p.s_g4) / nnorm(4);
-        dn[5] = (2.0 * ((double)gL[1] + gL[2]) - ((double)gL[3] + gL[4] + gL[5] + gL[6])) * (1.0 - p.s_g5) / nnorm(5);
-        dn[6] = (((double)gL[3] + gL[4]) - ((double)gL[5] + gL[6])) * (1.0 - p.s_g5) / nnorm(6);
-#pragma unroll
-        for (int i = 0; i < 7; ++i)
-#pragma unroll
-            for (int kk = 1; kk < 7; ++kk) gh[i] += npoly(kk, i) * dn[kk];
+        const float TL = Th + p.Tm;
+        const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
+        constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+        constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+        const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
+        float cn[7];
+        cn[0] = 0.0f;
+        cn[1] = ra * ((gL[1] - gL[2]) - ux * TL) * i1;
+        cn[2] = ra * ((gL[3] - gL[4]) - uy * TL) * i1;
+        cn[3] = ra * ((gL[5] - gL[6]) - uz * TL) * i1;
+        cn[4] = r4 * (6.0f * gL[0] - (gL[1] + gL[2] + gL[3] + gL[4] + gL[5] + gL[6]) - 0.75f * Th) * i4;
+        cn[5] = r5 * (2.0f * (gL[1] + gL[2]) - (gL[3] + gL[4] + gL[5] + gL[6])) * i5;
+        cn[6] = r5 * ((gL[3] + gL[4]) - (gL[5] + gL[6])) * i6;
+        add_back7<0>(gh, cn);
     }
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gpost[(long long)i * p.ncols + col] = (float)gh[i];
+    for (int i = 0; i < 7; ++i) gpost[(long long)i * p.ncols + col] = gh[i];
 }
 
 // ------------------------------------------------------------------ flip
@@ -301,13 +359,31 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
 // old flags (streaming if the upstream node was liquid, bounce-back if not)
 // and zero to a newly liquid node.  A link whose two ends both flipped is
 // handled once, by the end with the lower node index.
+//
+// Every column also records the minimum and maximum of the new liquid counts
+// over its 3x3 neighbourhood (min << 16 | max) for the interior and
+// deep-solid tests of the next stream-collide.  do_flip = 0 only records.
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const int *__restrict__ js_old,
-                                              const int *__restrict__ js_new, int inflight) {
+                                              const int *__restrict__ js_new, int *__restrict__ nb_new,
+                                              int inflight, int do_flip) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= p.ncols) return;
+    {
+        const int pp = col % p.P1, q = col / p.P1;
+        int mn = 1 << 15, mx = 0;
+        for (int dq = -1; dq <= 1; ++dq)
+            for (int dp = -1; dp <= 1; ++dp) {
+                const int p2 = pp + dp, q2 = q + dq;
+                if (p2 < 0 || p2 >= p.P1 || q2 < 0 || q2 >= p.P2) continue;
+                const int v = js_new[q2 * p.P1 + p2];
+                mn = v < mn ? v : mn;
+                mx = v > mx ? v : mx;
+            }
+        nb_new[col] = (mn << 16) | mx;
+    }
     const int jo = js_old[col], jn = js_new[col];
-    if (jo == jn) return;
+    if (!do_flip || jo == jn) return;
     const int lo = jo < jn ? jo : jn, hi = jo < jn ? jn : jo;
     for (int j = lo; j < hi; ++j) {
         int x, y, z;
@@ -375,10 +451,13 @@ __global__ void __launch_bounds__(128) k_macro(KP p, const ST *__restrict__ F, c
 }
 
 // Natural (unshifted) distributions out, direction-major with stride N.
+// Solid nodes report f = 0; deep solid nodes (see deep_solid) report g at
+// rest at Tm, the value their slots would hold if they were updated.
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_state_out(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
-                                                   const int *__restrict__ js, const float *__restrict__ thw,
-                                                   int inflight, float *__restrict__ fo, float *__restrict__ go) {
+                                                   const int *__restrict__ js, const int *__restrict__ nb,
+                                                   const float *__restrict__ thw, int inflight,
+                                                   float *__restrict__ fo, float *__restrict__ go) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -387,7 +466,12 @@ __global__ void __launch_bounds__(128) k_state_out(KP p, const ST *__restrict__ 
     const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
     if (go) {
         float g[7];
-        gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
+        if (a >= js[col] && deep_solid(p, a, nb[col])) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) g[i] = 0.0f;
+        } else {
+            gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
+        }
 #pragma unroll
         for (int i = 0; i < 7; ++i) go[i * p.N + c] = g[i] + w7(i) * p.Tm;
     }
@@ -400,8 +484,10 @@ __global__ void __launch_bounds__(128) k_state_out(KP p, const ST *__restrict__ 
     }
 }
 
-// Natural distributions in; leaves the natural layout.  Solid nodes get
-// fh = 0.
+// Natural distributions in; leaves the natural layout.  A solid node's own
+// populations never enter the method (its post-collision values are reset
+// every step), so solid nodes are stored at rest: fh = 0 and gh = 0
+// (g at rest at Tm).
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_state_in(KP p, ST *__restrict__ F, ST *__restrict__ G,
                                                   const int *__restrict__ js, const float *__restrict__ fi,
@@ -412,14 +498,13 @@ __global__ void __launch_bounds__(128) k_state_in(KP p, ST *__restrict__ F, ST *
     if (x >= p.nx || y >= p.ny) return;
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
+    const bool liq = a < js[col];
     if (gi)
 #pragma unroll
-        for (int i = 0; i < 7; ++i) Store<ST>::st(G + i * p.ld + c, gi[i * p.N + c] - w7(i) * p.Tm);
-    if (fi) {
-        const bool liq = a < js[col];
+        for (int i = 0; i < 7; ++i) Store<ST>::st(G + i * p.ld + c, liq ? gi[i * p.N + c] - w7(i) * p.Tm : 0.0f);
+    if (fi)
 #pragma unroll
         for (int i = 0; i < 19; ++i) Store<ST>::st(F + i * p.ld + c, liq ? fi[i * p.N + c] - w19(i) : 0.0f);
-    }
 }
 
 // Initial state: fh = 0 everywhere (rest, rho = 1); gh = w (T(a) - Tm) with

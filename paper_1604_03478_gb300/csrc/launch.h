@@ -12,6 +12,8 @@ struct Bufs {
     void *F, *G;                 // shifted distributions, 19 and 7 arrays of ld elements
     const int *js;               // liquid-node count per column (current flags)
     int *js_next;
+    const int *nb;               // 3x3 min/max of js (min << 16 | max), current
+    int *nb_next;
     const double *s;             // front per column (current)
     double *s_next;
     float *gpost;                // ghost-node post-collision g, 7 x ncols
@@ -22,7 +24,7 @@ struct Bufs {
 template <typename ST> struct Launch {
     static cudaError_t stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st);
     static cudaError_t front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st);
-    static cudaError_t flip(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st);
+    static cudaError_t flip(const KP &p, int face, int inflight, int do_flip, const Bufs &b, cudaStream_t st);
     static cudaError_t macro(const KP &p, int face, int inflight, const Bufs &b, float *T, float *u, cudaStream_t st);
     static cudaError_t state_out(const KP &p, int face, int inflight, const Bufs &b, float *f, float *g, cudaStream_t st);
     static cudaError_t state_in(const KP &p, int face, const Bufs &b, const float *f, const float *g, cudaStream_t st);

@@ -12,11 +12,11 @@ cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Buf
     dim3 grd = node_grid(p, blk);
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost, b.thw_rd, b.thw_wr);
-        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost);
+        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr);
+        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
     } else {
-        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost, b.thw_rd, b.thw_wr);
-        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.gpost);
+        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr);
+        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
     }
     return cudaGetLastError();
 }
@@ -33,11 +33,11 @@ cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, con
 }
 
 template <typename ST>
-cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st) {
+cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, int do_flip, const Bufs &b, cudaStream_t st) {
     dim3 blk(128), grd((p.ncols + 127) / 128);
     ST *F = (ST *)b.F;
-    if (face == 0) k_flip<ST, 0><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, inflight);
-    else k_flip<ST, 1><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, inflight);
+    if (face == 0) k_flip<ST, 0><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
+    else k_flip<ST, 1><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
     return cudaGetLastError();
 }
 
@@ -54,8 +54,8 @@ template <typename ST>
 cudaError_t Launch<ST>::state_out(const KP &p, int face, int inflight, const Bufs &b, float *f, float *g, cudaStream_t st) {
     dim3 blk = node_block(p), grd = node_grid(p, blk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
-    if (face == 0) k_state_out<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, f, g);
-    else k_state_out<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, f, g);
+    if (face == 0) k_state_out<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.thw_rd, inflight, f, g);
+    else k_state_out<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.thw_rd, inflight, f, g);
     return cudaGetLastError();
 }
 

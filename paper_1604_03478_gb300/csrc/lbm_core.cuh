@@ -105,6 +105,10 @@ struct KP {
     float s_alpha, s_g4, s_g5;
     double Tm_d, Th_d;
     double coef;      // alpha Ste / (Th - Tm): Eq. 6 front speed per unit -dT/da
+    int skip_deep;    // Tc == Tm: deep solid nodes need no update
+    // element offsets of the interior odd step, relative to node c:
+    // f_i is pulled from slot opp(i) of c - e_i and pushed to slot i of c + e_i
+    long long fin[19], fout[19], gin[7], gout[7];
 };
 
 // ------------------------------------------------------------ load/store
@@ -119,48 +123,77 @@ template <> struct Store<__half> {
 };
 
 // ----------------------------------------------- compile-time transforms
-// acc + sum_i mpoly(K, i) v[i] over the nonzero coefficients only.
-template <int K, int I>
-__device__ __forceinline__ float mrow(const float (&v)[19], float acc) {
-    if constexpr (I == 19) {
+// The 18 moving velocities form 9 opposite pairs (i, opp(i)); pair P has
+// first member pf(P).  A moment row is even or odd in e, so it sees a pair
+// only through S = f_i + f_opp(i) (even rows) or D = f_i - f_opp(i) (odd
+// rows), which halves the work of m = M f and of f += M^T c.
+__host__ __device__ constexpr int pf(int P) {
+    return P == 0 ? 1 : P == 1 ? 3 : P == 2 ? 5 : P == 3 ? 7 : P == 4 ? 8 : P == 5 ? 11 : P == 6 ? 12
+         : P == 7 ? 15 : 16;
+}
+__host__ __device__ constexpr bool row_odd(int k) {
+    return (k >= 3 && k <= 8) || k >= 16;
+}
+
+// acc + sum over pairs of mpoly(K, pf(P)) v[P], nonzero coefficients only.
+template <int K, int P>
+__device__ __forceinline__ float prow(const float (&v)[9], float acc) {
+    if constexpr (P == 9) {
         return acc;
     } else {
-        constexpr int m = mpoly(K, I);
-        if constexpr (m == 0) return mrow<K, I + 1>(v, acc);
-        else if constexpr (m == 1) return mrow<K, I + 1>(v, acc + v[I]);
-        else if constexpr (m == -1) return mrow<K, I + 1>(v, acc - v[I]);
-        else return mrow<K, I + 1>(v, fmaf((float)m, v[I], acc));
+        constexpr int m = mpoly(K, pf(P));
+        if constexpr (m == 0) return prow<K, P + 1>(v, acc);
+        else if constexpr (m == 1) return prow<K, P + 1>(v, acc + v[P]);
+        else if constexpr (m == -1) return prow<K, P + 1>(v, acc - v[P]);
+        else return prow<K, P + 1>(v, fmaf((float)m, v[P], acc));
     }
 }
 
-// acc + sum_k mpoly(k, I) c[k] over k with nonzero coefficients, skipping
-// the rows whose update is identically zero (mass; x and y momentum).
-template <int I, int K>
-__device__ __forceinline__ float mcol(const float (&c)[19], float acc) {
+// m[K] for all rows from the rest population and the pair sums/differences.
+template <int K>
+__device__ __forceinline__ void moments_pairs(float f0, const float (&S)[9], const float (&D)[9], float (&m)[19]) {
+    if constexpr (K < 19) {
+        if constexpr (row_odd(K)) m[K] = prow<K, 0>(D, -0.0f);
+        else m[K] = prow<K, 0>(S, (float)mpoly(K, 0) * f0);
+        moments_pairs<K + 1>(f0, S, D, m);
+    }
+}
+
+// Sum over rows K.. of mpoly(k, I) c[k] restricted to rows of parity ODD,
+// skipping rows whose update is identically zero (mass; x and y momentum).
+template <int I, int K, bool ODD>
+__device__ __forceinline__ float pcol(const float (&c)[19], float acc) {
     if constexpr (K == 19) {
         return acc;
     } else {
         constexpr int m = mpoly(K, I);
-        if constexpr (m == 0 || K == 0 || K == 3 || K == 5) return mcol<I, K + 1>(c, acc);
-        else if constexpr (m == 1) return mcol<I, K + 1>(c, acc + c[K]);
-        else if constexpr (m == -1) return mcol<I, K + 1>(c, acc - c[K]);
-        else return mcol<I, K + 1>(c, fmaf((float)m, c[K], acc));
+        if constexpr (m == 0 || K == 0 || K == 3 || K == 5 || row_odd(K) != ODD) return pcol<I, K + 1, ODD>(c, acc);
+        else if constexpr (m == 1) return pcol<I, K + 1, ODD>(c, acc + c[K]);
+        else if constexpr (m == -1) return pcol<I, K + 1, ODD>(c, acc - c[K]);
+        else return pcol<I, K + 1, ODD>(c, fmaf((float)m, c[K], acc));
     }
 }
 
+// f += M^T c, pair by pair: f_i += E + O, f_opp(i) += E - O.
+template <int P>
+__device__ __forceinline__ void add_back_pairs(float (&f)[19], const float (&c)[19]) {
+    if constexpr (P < 9) {
+        constexpr int i = pf(P), j = opp(pf(P));
+        const float E = pcol<i, 0, false>(c, -0.0f);
+        const float O = pcol<i, 0, true>(c, -0.0f);
+        f[i] += E + O;
+        f[j] += E - O;
+        add_back_pairs<P + 1>(f, c);
+    }
+}
+
+// c[k] = d[k] / |row k|^2 with the reciprocal formed at compile time.
 template <int K>
-__device__ __forceinline__ void moments_from(const float (&f)[19], float (&m)[19]) {
+__device__ __forceinline__ void scale_by_inverse_norms(const float (&d)[19], float (&c)[19]) {
     if constexpr (K < 19) {
-        m[K] = mrow<K, 0>(f, -0.0f);
-        moments_from<K + 1>(f, m);
-    }
-}
-
-template <int I>
-__device__ __forceinline__ void add_back(float (&f)[19], const float (&c)[19]) {
-    if constexpr (I < 19) {
-        f[I] = mcol<I, 0>(c, f[I]);
-        add_back<I + 1>(f, c);
+        constexpr float inv = 1.0f / (float)mnorm(K);
+        c[K] = d[K] * inv;
+        scale_by_inverse_norms<K + 1>(d, c);
     }
 }
 
@@ -212,8 +245,13 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
     float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
     const float T = Th + p.Tm;
     const float Fz = p.gbeta * Th;
-    float m[19];
-    moments_from<0>(f, m);
+    float m[19], S[9], D[9];
+#pragma unroll
+    for (int P = 0; P < 9; ++P) {
+        S[P] = f[pf(P)] + f[opp(pf(P))];
+        D[P] = f[pf(P)] - f[opp(pf(P))];
+    }
+    moments_pairs<0>(f[0], S, D, m);
     const float rho_h = m[0];
     const float ux = m[3], uy = m[5], uz = m[7] + 0.5f * Fz;
     const float uu = ux * ux + uy * uy + uz * uz;
@@ -239,22 +277,24 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
     d[17] = -p.s_m * m[17];
     d[18] = -p.s_m * m[18];
     float c[19];
-#pragma unroll
-    for (int k = 0; k < 19; ++k) c[k] = d[k] * (1.0f / (float)mnorm(k));
-    add_back<0>(f, c);
+    scale_by_inverse_norms<0>(d, c);
+    f[0] = pcol<0, 0, false>(c, f[0]);
+    add_back_pairs<0>(f, c);
 
     float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
     float n4 = 6.0f * g[0] - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6]);
     float n5 = 2.0f * (g[1] + g[2]) - (g[3] + g[4] + g[5] + g[6]);
     float n6 = (g[3] + g[4]) - (g[5] + g[6]);
+    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
     float cn[7];
     cn[0] = 0.0f;
-    cn[1] = -p.s_alpha * (n1 - ux * T) * (1.0f / (float)nnorm(1));
-    cn[2] = -p.s_alpha * (n2 - uy * T) * (1.0f / (float)nnorm(2));
-    cn[3] = -p.s_alpha * (n3 - uz * T) * (1.0f / (float)nnorm(3));
-    cn[4] = -p.s_g4 * (n4 - 0.75f * Th) * (1.0f / (float)nnorm(4));
-    cn[5] = -p.s_g5 * n5 * (1.0f / (float)nnorm(5));
-    cn[6] = -p.s_g5 * n6 * (1.0f / (float)nnorm(6));
+    cn[1] = -p.s_alpha * (n1 - ux * T) * i1;
+    cn[2] = -p.s_alpha * (n2 - uy * T) * i1;
+    cn[3] = -p.s_alpha * (n3 - uz * T) * i1;
+    cn[4] = -p.s_g4 * (n4 - 0.75f * Th) * i4;
+    cn[5] = -p.s_g5 * n5 * i5;
+    cn[6] = -p.s_g5 * n6 * i6;
     add_back7<0>(g, cn);
     if (uout) { uout[0] = ux; uout[1] = uy; uout[2] = uz; }
 }
@@ -286,11 +326,10 @@ template <int FACE> __device__ __forceinline__ bool liquid_at(const KP &p, const
 // Wall crossed by the D3Q7 link that leaves node (x,y,z) along direction i
 // (i.e. x + t_i is outside): 1 heated wall, 2 opposite isothermal wall,
 // 3 adiabatic wall.  Only meaningful when x + t_i is outside.
-template <int FACE> __device__ __forceinline__ int wall_of_link(int i) {
+template <int FACE> __host__ __device__ constexpr int wall_of_link(int i) {
     // the heating axis is y (directions 3, 4) or z (5, 6); the heated wall is
     // at coordinate 0, reached going in the negative direction
-    if (FACE == 0) return i == 4 ? 1 : (i == 3 ? 2 : 3);
-    return i == 6 ? 1 : (i == 5 ? 2 : 3);
+    return FACE == 0 ? (i == 4 ? 1 : (i == 3 ? 2 : 3)) : (i == 6 ? 1 : (i == 5 ? 2 : 3));
 }
 
 }  // namespace lbm

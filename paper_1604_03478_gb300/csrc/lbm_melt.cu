@@ -67,6 +67,7 @@ lbm_status derive(const lbm_melt_grid *g, double Ra, double Pr, double Ste, doub
     d.P1 = g->nx;
     d.P2 = g->heated_face == 0 ? g->nz : g->ny;
     if (d.H < 4) return fail("cavity length along the heating axis must be >= 4");
+    if (d.H > 32767) return fail("cavity length along the heating axis must be <= 32767");
     d.N = (long long)g->nx * g->ny * g->nz;
     d.ncols = (long long)d.P1 * d.P2;
     if (d.N > (1LL << 31) - 1) return fail("too many nodes");
@@ -122,6 +123,7 @@ struct lbm_melt {
     int device;
     void *F, *G;
     int *js[2];
+    int *nb[2];
     double *s[2];
     int cur;
     float *gpost;
@@ -167,6 +169,8 @@ Bufs bufs(lbm_melt *h) {
     b.G = h->G;
     b.js = h->js[h->cur];
     b.js_next = h->js[1 - h->cur];
+    b.nb = h->nb[h->cur];
+    b.nb_next = h->nb[1 - h->cur];
     b.s = h->s[h->cur];
     b.s_next = h->s[1 - h->cur];
     b.gpost = h->gpost;
@@ -180,10 +184,12 @@ Bufs bufs(lbm_melt *h) {
     ((h)->precision == 1 ? lbm::Launch<__half>::method(__VA_ARGS__)                  \
                          : lbm::Launch<float>::method(__VA_ARGS__))
 
-// Prepare js from s and the ghost nodes from the state (front held).
+// Prepare js from s, its 3x3 bounds and the ghost nodes from the state
+// (front held, no flip).
 lbm_status refresh_front(lbm_melt *h) {
     Bufs b = bufs(h);
     CK(LAUNCH(h, front, h->kp, h->face, h->inflight, 0, b, h->stream), "front refresh");
+    CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, 0, b, h->stream), "neighbour bounds");
     h->cur ^= 1;
     return LBM_OK;
 }
@@ -206,7 +212,7 @@ lbm_status check_status(lbm_melt *h) {
 void free_all(lbm_melt *h) {
     cudaFree(h->F);
     cudaFree(h->G);
-    for (int k = 0; k < 2; ++k) { cudaFree(h->js[k]); cudaFree(h->s[k]); }
+    for (int k = 0; k < 2; ++k) { cudaFree(h->js[k]); cudaFree(h->nb[k]); cudaFree(h->s[k]); }
     cudaFree(h->gpost);
     cudaFree(h->thw_cur);
     cudaFree(h->thw_prev);
@@ -301,6 +307,20 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     p.s_alpha = (float)d.s_alpha; p.s_g4 = (float)d.s_g4; p.s_g5 = (float)d.s_g5;
     p.Tm_d = Tm; p.Th_d = Th;
     p.coef = Ste > 0.0 ? d.alpha * Ste / (Th - Tm) : 0.0;
+    p.skip_deep = (Tc == Tm) ? 1 : 0;
+    {
+        const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+        for (int i = 0; i < 19; ++i) {
+            const long long off = lbm::ex(i) + lbm::ey(i) * sy + lbm::ez(i) * sz;
+            p.fin[i] = lbm::opp(i) * p.ld - off;
+            p.fout[i] = i * p.ld + off;
+        }
+        for (int i = 0; i < 7; ++i) {
+            const long long off = lbm::tx(i) + lbm::ty(i) * sy + lbm::tz(i) * sz;
+            p.gin[i] = lbm::opp7(i) * p.ld - off;
+            p.gout[i] = i * p.ld + off;
+        }
+    }
     auto fail = [&](lbm_status s) { free_all(h); delete h; return s; };
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(LBM_ECUDA);
     const size_t es = h->precision == 1 ? sizeof(__half) : sizeof(float);
@@ -308,6 +328,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     const size_t nc = (size_t)d.ncols;
     struct { void **p; size_t b; } allocs[] = {
         {&h->F, nF}, {&h->G, nG}, {(void **)&h->js[0], nc * 4}, {(void **)&h->js[1], nc * 4},
+        {(void **)&h->nb[0], nc * 4}, {(void **)&h->nb[1], nc * 4},
         {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
         {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
         {(void **)&h->sum_dev, 8}};
@@ -332,6 +353,8 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     if (e == cudaSuccess) e = cudaMemsetAsync(h->F, 0, nF, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->G, 0, nG, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->js[0], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[0], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[1], 0, nc * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->gpost, 0, 7 * nc * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) {
@@ -395,7 +418,7 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         if (odd) h->thw_pending = 0;
         b = bufs(h);
         CK(LAUNCH(h, front, h->kp, h->face, h->inflight, 1, b, h->stream), "front");
-        CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, b, h->stream), "flip");
+        CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, 1, b, h->stream), "flip");
         h->cur ^= 1;
         h->steps++;
     }

@@ -95,9 +95,11 @@ def test_steps_from_random_state(lib, orc, face, nsteps):
     o.step(nsteps)
     fg, gg, sg = gpu.get_state()
     fo, go, so = o.get_state()
+    liq = fo.any(axis=0)  # solid nodes hold no f; their g never enters the method
     np.testing.assert_allclose(sg, so, atol=1e-7, rtol=0)
-    np.testing.assert_allclose(gg, go, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(gg[:, liq], go[:, liq], atol=2e-6, rtol=0)
     np.testing.assert_allclose(fg, fo, atol=2e-6, rtol=0)
+    _compare(gpu, o, tol_u=2e-6)
 
 
 @pytest.mark.parametrize("face", [0, 1])
@@ -119,14 +121,18 @@ def test_flips_after_even_and_odd_steps(lib, orc, face):
         o.step(1)
         fg, gg, sg = gpu.get_state()
         fo, go, so = o.get_state()
+        liq = fo.any(axis=0)
         np.testing.assert_allclose(sg, so, atol=1e-7, rtol=0)
         np.testing.assert_allclose(fg, fo, atol=2e-6, rtol=0)
-        np.testing.assert_allclose(gg, go, atol=2e-6, rtol=0)
+        np.testing.assert_allclose(gg[:, liq], go[:, liq], atol=2e-6, rtol=0)
+        _compare(gpu, o, tol_u=2e-6)
         if n == 1:
             assert (np.ceil(so - 0.5) > js0).mean() > 0.5  # most columns flipped in the even step
 
 
 def test_state_roundtrip(lib, orc):
+    """set_state / get_state are inverse on liquid nodes, from the natural
+    layout and from the in-flight layout (solid nodes are stored at rest)."""
     gpu = lib(11, 12, 9, face=0, Ra=0.0, Ste=0.5, s_nu=1.2, s_alpha=1.0)
     o = orc.Oracle(11, 12, 9, face=0, Ra=0.0, Ste=0.5, s_nu=1.2, s_alpha=1.0)
     f, g, s = _random_state(o, 3, 2.0, 9.0)
@@ -137,10 +143,11 @@ def test_state_roundtrip(lib, orc):
     np.testing.assert_allclose(f2, f, atol=1e-7)
     gpu.step(1)  # values now in flight
     f3, g3, s3 = gpu.get_state()
+    liq = f3.any(axis=0)
     gpu.set_state(f3, g3, s3)
     f4, g4, s4 = gpu.get_state()
     np.testing.assert_allclose(f4, f3, atol=1e-7)
-    np.testing.assert_allclose(g4, g3, atol=1e-7)
+    np.testing.assert_allclose(g4[:, liq], g3[:, liq], atol=1e-7)
 
 
 @pytest.mark.parametrize("when", [0, 1])
