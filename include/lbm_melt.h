@@ -129,6 +129,21 @@ lbm_status lbm_melt_step(lbm_melt *h, long long n);
 lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
                         int ptr_kind);
 
+/* Same outputs as lbm_melt_get, without allocating anything.  The paper has
+   no counterpart: this serves callers that cannot let a library allocate
+   device memory (a time-critical loop in which a cudaMalloc would synchronise
+   the device, or an application whose own pool allocator owns all device
+   memory).  Host-bound results are staged through a fixed array that the
+   library holds on every GPU that loads it until the process exits, sized
+   for at most 2097152 nodes (128^3); a larger cavity is rejected with
+   LBM_EINVAL.  The handle's device must be current.  The first call on a
+   device performs a one-time set-up (it looks up the array's device
+   address); make that first call before any stream capture.  Every call
+   shares the array: calls whose work overlaps on the GPU race.  Calls no
+   cudaMalloc, cudaFree or allocating library routine.  Synchronises. */
+lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
+                                int ptr_kind);
+
 /* Distributions in natural form (post-streaming, pre-collision; f_i and g_i,
    not shifted), direction-major: f[i*N + node], g[i*N + node]; solid nodes
    report f = 0, and solid nodes whose neighbourhood is all solid report g at

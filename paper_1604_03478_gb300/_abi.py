@@ -62,6 +62,7 @@ def load() -> C.CDLL:
                                       C.c_double, C.c_double, C.POINTER(lbm_melt_rates), vp, C.POINTER(vp)]),
         "lbm_melt_step": (C.c_int, [vp, C.c_longlong]),
         "lbm_melt_get": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+        "lbm_melt_get_noalloc": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "lbm_melt_get_state": (C.c_int, [vp, vp, vp, vp, C.c_int]),
         "lbm_melt_set_state": (C.c_int, [vp, vp, vp, vp, C.c_int]),
         "lbm_melt_set_hot_wall": (C.c_int, [vp, vp, C.c_int]),

@@ -580,3 +580,62 @@ LBM_API lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *laun
     if (reset) h->ev_used = 0;
     return LBM_OK;
 }
+
+// ------------------------------------------------------------------------
+// Read-back without allocation.
+//
+// lbm_melt_get stages host-bound T and u in device buffers it allocates per
+// call.  Some callers cannot let a library allocate: a real-time driver loop
+// in which a cudaMalloc would synchronise the device, or an application that
+// gives all device memory to its own pool allocator.  lbm_melt_get_noalloc
+// stages through the fixed array below instead.  The array lives in every GPU
+// that loads the library until the process exits.  All calls share it, so
+// calls whose work overlaps on the GPU race with each other.
+static const long long kNoallocMaxNodes = 2097152;  // 128^3: 16 bytes per node (T and u)
+static __device__ __align__(256) unsigned char g_noalloc_stage[kNoallocMaxNodes * 16 + 256];
+
+namespace {
+const int kMaxDevices = 64;
+void *g_noalloc_dev[kMaxDevices];  // device address of the array, per device (null: not looked up yet)
+}  // namespace
+
+LBM_API lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
+                                        int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    const KP &p = h->kp;
+    const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
+    if (p.N > kNoallocMaxNodes)
+        return set_err(h, LBM_EINVAL, "lbm_melt_get_noalloc stages at most %lld nodes; this cavity has %lld",
+                       kNoallocMaxNodes, p.N);
+    int dev = -1;
+    CK(cudaGetDevice(&dev), "get device");
+    if (dev != h->device || dev < 0 || dev >= kMaxDevices)
+        return set_err(h, LBM_EINVAL, "make the handle's device (%d) current before lbm_melt_get_noalloc", h->device);
+    if (!g_noalloc_dev[dev]) {
+        // one-time set-up on this device (the device is current): the host-side
+        // name of the array is only a stand-in, so look up its device address
+        void *ptr = nullptr;
+        CK(cudaGetSymbolAddress(&ptr, g_noalloc_stage), "staging array address");
+        g_noalloc_dev[dev] = ptr;
+    }
+    unsigned char *stage = (unsigned char *)g_noalloc_dev[dev];
+    float *Td = ptr_kind ? T : (float *)stage;
+    float *ud = ptr_kind ? u : (float *)(stage + N * 4);
+    double *lfd = ptr_kind ? liquid_fraction : (double *)(stage + kNoallocMaxNodes * 16);
+    if (T || u) {
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, macro, p, h->face, h->inflight, b, T ? Td : nullptr, u ? ud : nullptr, h->stream), "macro");
+        if (!ptr_kind) {
+            if (T) CK(cudaMemcpyAsync(T, Td, N * 4, cudaMemcpyDeviceToHost, h->stream), "copy T");
+            if (u) CK(cudaMemcpyAsync(u, ud, 3 * N * 4, cudaMemcpyDeviceToHost, h->stream), "copy u");
+        }
+    }
+    if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream), "copy S");
+    if (liquid_fraction) {
+        k_sum<<<1, 1024, 0, h->stream>>>(h->s[h->cur], (long long)nc, 1.0 / ((double)p.H * (double)nc), lfd);
+        CK(cudaGetLastError(), "sum");
+        if (!ptr_kind) CK(cudaMemcpyAsync(liquid_fraction, lfd, 8, cudaMemcpyDeviceToHost, h->stream), "copy lf");
+    }
+    return check_status(h);
+}
