@@ -164,6 +164,25 @@ lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *g, const
    next step's streaming. */
 lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, int ptr_kind);
 
+/* FP64 totals of the current state (paper §3.1 and Fig. 4(d): the liquid
+   fraction; energy and mass balances): out[0] liquid fraction, out[1]
+   sum over liquid nodes of (T - Tm), out[2] sum over liquid nodes of
+   (rho - 1), out[3] number of liquid nodes, out[4] max |u| over liquid nodes,
+   out[5] sum of S over columns.  The heat content relative to solid at Tm is
+   out[1] + (Th - Tm) / Ste * out[5].  Deterministic (fixed reduction order).
+   Synchronises. */
+lbm_status lbm_melt_totals(lbm_melt *h, double *out, int ptr_kind);
+
+/* Record the totals every `every` steps (0 turns recording off) into a ring
+   of `capacity` rows of 7 doubles {steps, out[0..5] of lbm_melt_totals},
+   filled on the device inside lbm_melt_step.  Clears earlier rows. */
+lbm_status lbm_melt_set_report(lbm_melt *h, long long every, long long capacity);
+
+/* Copy up to max_rows recorded rows (oldest kept first) to host memory;
+   *n_rows receives how many.  rows = NULL asks how many rows are kept.
+   Synchronises. */
+lbm_status lbm_melt_get_report(lbm_melt *h, double *rows, long long max_rows, long long *n_rows);
+
 /* Derived quantities and counters of a handle. */
 lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info);
 

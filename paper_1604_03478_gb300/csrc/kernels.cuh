@@ -525,4 +525,85 @@ __global__ void __launch_bounds__(128) k_init(KP p, ST *__restrict__ F, ST *__re
     for (int i = 0; i < 7; ++i) Store<ST>::st(G + i * p.ld + c, w7(i) * dT);
 }
 
+// ------------------------------------------------------ FP64 reductions
+// Block partials of the liquid-node totals: sum (T - Tm), sum (rho - 1),
+// count, max |u|^2.  Fixed block and thread order: deterministic.
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(256) k_totals_part(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+                                                     const int *__restrict__ js, const float *__restrict__ thw,
+                                                     int inflight, double *__restrict__ part) {
+    __shared__ double sh[4][256];
+    double sT = 0.0, sr = 0.0, n = 0.0, umax = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < p.N; c += stride) {
+        const int x = (int)(c % p.nx), y = (int)((c / p.nx) % p.ny), z = (int)(c / ((long long)p.nx * p.ny));
+        if (axial<FACE>(x, y, z) >= js[column<FACE>(p, x, y, z)]) continue;
+        float g[7], f[19];
+        gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
+        gather_f<ST, FACE>(p, F, js, x, y, z, inflight != 0, f);
+        float Th = 0.0f, rh = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) Th += g[i];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) { rh += f[i]; ux += ex(i) * f[i]; uy += ey(i) * f[i]; uz += ez(i) * f[i]; }
+        uz += 0.5f * p.gbeta * Th;
+        sT += Th;
+        sr += rh;
+        n += 1.0;
+        const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+        umax = u2 > umax ? u2 : umax;
+    }
+    sh[0][threadIdx.x] = sT; sh[1][threadIdx.x] = sr; sh[2][threadIdx.x] = n; sh[3][threadIdx.x] = umax;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Final pass in one block: out = {liquid fraction, sum (T - Tm), sum (rho - 1),
+// liquid nodes, max |u|, sum s}; with t >= 0 also writes the time first.
+static __global__ void __launch_bounds__(256) k_totals_final(const double *__restrict__ part, int nparts,
+                                                      const double *__restrict__ s, int ncols, double H,
+                                                      double t, double *__restrict__ out) {
+    __shared__ double sh[5][256];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, ss = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        a0 += part[b * 4];
+        a1 += part[b * 4 + 1];
+        a2 += part[b * 4 + 2];
+        a3 = fmax(a3, part[b * 4 + 3]);
+    }
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) ss += s[c];
+    sh[0][threadIdx.x] = a0; sh[1][threadIdx.x] = a1; sh[2][threadIdx.x] = a2; sh[3][threadIdx.x] = a3;
+    sh[4][threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+            sh[4][threadIdx.x] += sh[4][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double *o = out;
+        if (t >= 0.0) *o++ = t;
+        o[0] = sh[4][0] / (H * (double)ncols);
+        o[1] = sh[0][0];
+        o[2] = sh[1][0];
+        o[3] = sh[2][0];
+        o[4] = sqrt(sh[3][0]);
+        o[5] = sh[4][0];
+    }
+}
+
 }  // namespace lbm

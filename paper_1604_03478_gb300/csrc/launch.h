@@ -29,6 +29,8 @@ template <typename ST> struct Launch {
     static cudaError_t state_out(const KP &p, int face, int inflight, const Bufs &b, float *f, float *g, cudaStream_t st);
     static cudaError_t state_in(const KP &p, int face, const Bufs &b, const float *f, const float *g, cudaStream_t st);
     static cudaError_t init(const KP &p, int face, const Bufs &b, const float *Tprof, cudaStream_t st);
+    static cudaError_t totals(const KP &p, int face, int inflight, const Bufs &b, double *part, int nparts,
+                              double t, double *out, cudaStream_t st);
 };
 
 // Block shape for the per-node kernels: 128 threads, x-major.

@@ -77,4 +77,14 @@ cudaError_t Launch<ST>::init(const KP &p, int face, const Bufs &b, const float *
     return cudaGetLastError();
 }
 
+template <typename ST>
+cudaError_t Launch<ST>::totals(const KP &p, int face, int inflight, const Bufs &b, double *part, int nparts,
+                               double t, double *out, cudaStream_t st) {
+    const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
+    if (face == 0) k_totals_part<ST, 0><<<nparts, 256, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, part);
+    else k_totals_part<ST, 1><<<nparts, 256, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, part);
+    k_totals_final<<<1, 256, 0, st>>>(part, nparts, b.s, p.ncols, (double)p.H, t, out);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

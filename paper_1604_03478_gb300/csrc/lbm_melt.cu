@@ -23,6 +23,7 @@ using lbm::KP;
 namespace {
 
 const double CS2T = 0.25;  // D3Q7 pseudo sound speed squared (w0 = 1/4)
+const int kRedBlocks = 608;  // partial blocks of the FP64 totals (4 per SM of a GB300)
 
 struct Derived {
     int H, P1, P2;
@@ -131,6 +132,11 @@ struct lbm_melt {
     int thw_pending;   // set_hot_wall happened while values were in flight
     int *status_dev;
     double *sum_dev;
+    double *red_part;  // scratch: per-block partials of the FP64 totals
+    int nred;          // number of partial blocks
+    double *totals_dev;  // 6 doubles
+    double *report;    // ring of report rows (7 doubles: t, totals)
+    long long report_every, report_cap, report_rows;
     int inflight;      // last stream-collide was an even (local) step
     long long steps;
     size_t bytes;
@@ -218,6 +224,9 @@ void free_all(lbm_melt *h) {
     cudaFree(h->thw_prev);
     cudaFree(h->status_dev);
     cudaFree(h->sum_dev);
+    cudaFree(h->red_part);
+    cudaFree(h->totals_dev);
+    cudaFree(h->report);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
 }
@@ -331,7 +340,8 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         {(void **)&h->nb[0], nc * 4}, {(void **)&h->nb[1], nc * 4},
         {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
         {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
-        {(void **)&h->sum_dev, 8}};
+        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 6 * 8}};
+    h->nred = kRedBlocks;
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.b);
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
@@ -421,6 +431,58 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, 1, b, h->stream), "flip");
         h->cur ^= 1;
         h->steps++;
+        if (h->report_every > 0 && h->steps % h->report_every == 0) {
+            double *row = h->report + 7 * (h->report_rows % h->report_cap);
+            b = bufs(h);
+            CK(LAUNCH(h, totals, h->kp, h->face, h->inflight, b, h->red_part, h->nred, (double)h->steps, row,
+                      h->stream), "report totals");
+            h->report_rows++;
+        }
+    }
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_totals(lbm_melt *h, double *out, int ptr_kind) {
+    if (!h || !out) return LBM_EINVAL;
+    Bufs b = bufs(h);
+    CK(LAUNCH(h, totals, h->kp, h->face, h->inflight, b, h->red_part, h->nred, -1.0, h->totals_dev, h->stream),
+       "totals");
+    CK(cudaMemcpyAsync(out, h->totals_dev, 6 * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream), "copy totals");
+    return check_status(h);
+}
+
+LBM_API lbm_status lbm_melt_set_report(lbm_melt *h, long long every, long long capacity) {
+    if (!h || every < 0 || (every > 0 && capacity < 1)) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    cudaFree(h->report);
+    h->report = nullptr;
+    h->report_every = 0;
+    h->report_cap = 0;
+    h->report_rows = 0;
+    if (every == 0) return LBM_OK;
+    CK(cudaMalloc(&h->report, (size_t)capacity * 7 * 8), "alloc report");
+    h->report_every = every;
+    h->report_cap = capacity;
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_get_report(lbm_melt *h, double *rows, long long max_rows, long long *n_rows) {
+    if (!h || !n_rows) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    const long long avail = h->report_rows < h->report_cap ? h->report_rows : h->report_cap;
+    if (!rows) {  // query: how many rows are kept
+        *n_rows = avail;
+        return LBM_OK;
+    }
+    const long long n = avail < max_rows ? avail : max_rows;
+    *n_rows = n;
+    if (n == 0) return LBM_OK;
+    // the oldest kept row first
+    const long long first = h->report_rows - avail;
+    for (long long r = 0; r < n; ++r) {
+        const long long slot = (first + r) % h->report_cap;
+        CK(cudaMemcpy(rows + 7 * r, h->report + 7 * slot, 7 * 8, cudaMemcpyDeviceToHost), "copy report");
     }
     return LBM_OK;
 }

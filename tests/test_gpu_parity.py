@@ -179,3 +179,27 @@ def test_fp16_storage_error(lib, orc):
     dT, dlf = np.abs(Tg - To).max(), abs(lfg - lfo)
     print("fp16 storage: max|dT| = %.3g, |dlf| = %.3g" % (dT, dlf))
     assert dT < 2e-2 and dlf < 2e-3
+
+
+def test_totals_and_report(lib, orc):
+    """FP64 totals (liquid fraction, energy and mass sums over liquid nodes)
+    against the oracle, and the on-device report ring."""
+    kw = dict(face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
+    gpu, o = _pair(lib, orc, (24, 20, 16), **kw)
+    gpu.set_report(10, 64)
+    gpu.step(50)
+    o.step(50)
+    t = gpu.totals()
+    i = o.info()
+    To, uo, So, lfo = o.get()
+    nl = i["n_liquid"]
+    assert t["n_liquid"] == nl
+    assert abs(t["liquid_fraction"] - lfo) <= TOL_LF
+    assert abs(t["sum_T_minus_Tm"] - i["sum_T_liquid"]) <= TOL_T * nl      # Tm = 0
+    assert abs(t["sum_rho_minus_1"] - (i["mass"] - nl)) <= 1e-5 * nl
+    assert abs(t["max_u"] - np.sqrt((uo ** 2).sum(-1)).max()) <= 1e-4
+    assert abs(t["sum_S"] - So.sum()) <= TOL_LF * So.size
+    rows = gpu.get_report()
+    np.testing.assert_array_equal(rows[:, 0], [10, 20, 30, 40, 50])
+    assert np.all(np.diff(rows[:, 1]) > 0)                                  # melting
+    np.testing.assert_array_equal(rows[-1, 1:], [t[k] for k in gpu.TOTAL_KEYS])
