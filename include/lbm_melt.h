@@ -189,6 +189,11 @@ lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info);
 /* Wait for the handle's stream; report a device-side error flag. */
 lbm_status lbm_melt_sync(lbm_melt *h);
 
+/* Block shape (bx threads along x, a multiple of 32; by along y; bx*by <=
+   128) of the stream-collide kernels; (0, 0) restores the default.  The
+   autotuner in the Python package picks it per cavity size and precision. */
+lbm_status lbm_melt_set_launch(lbm_melt *h, int bx, int by);
+
 /* Kernel timing: when enabled, each stream-collide launch is bracketed by
    CUDA events; lbm_melt_kernel_time returns (after synchronising) the summed
    milliseconds and the number of timed launches since the last reset. */
@@ -197,6 +202,60 @@ lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, in
 
 const char *lbm_melt_last_error(const lbm_melt *h);
 void lbm_melt_destroy(lbm_melt *h);
+
+/* ------------------------------------------------------------------ ensemble
+   A batch of independent cavities of uneven sizes and parameters advanced in
+   lockstep by one persistent kernel launch per run of steps: each step covers
+   the nodes of all cavities (fused stream-collide), then all their columns
+   (front update, Eq. 6), then the phase flips, separated by grid-wide
+   barriers whose waits are bounded (an exhausted wait ends the launch;
+   lbm_ensemble_sync then returns LBM_ETIMEOUT).  The launch is captured once
+   in a CUDA graph (graph_steps steps per replay) and replayed. */
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* One member cavity: the arguments of lbm_melt_create. */
+typedef struct {
+    lbm_melt_grid grid;
+    double Ra, Pr, Ste, Th, Tc, Tm;
+    lbm_melt_rates rates;
+} lbm_melt_case;
+
+/* Create n cavities (all with the same storage precision) on the current
+   device.  The ensemble runs on a stream of its own, ordered after the work
+   queued on cuda_stream at each call and before the work queued there
+   afterwards. */
+lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *cuda_stream, lbm_ensemble **out);
+
+/* Advance every member by nsteps steps.  Asynchronous. */
+lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps);
+
+/* Launch shape: threads per block (multiple of 32 in [32, 256]), nodes per
+   thread in the stream-collide phase (1, 2 or 4) and steps per graph replay
+   (even, >= 2).  The grid is the co-resident maximum for that shape. */
+lbm_status lbm_ensemble_set_launch(lbm_ensemble *e, int block, int nodes_per_thread, int graph_steps);
+
+/* Bound of a barrier wait, in polls (default 2^24, about a second). */
+lbm_status lbm_ensemble_set_barrier_timeout(lbm_ensemble *e, long long max_spins);
+
+/* Test hook for failure detection: one step in which block `block` never
+   arrives at the first barrier, so that the bounded waits of the others run
+   out and the launch returns; lbm_ensemble_sync then reports LBM_ETIMEOUT.
+   The members' states are not meaningful afterwards. */
+lbm_status lbm_ensemble_inject_barrier_fault(lbm_ensemble *e, int block);
+
+/* Wait for the ensemble; report a barrier timeout or a member's error. */
+lbm_status lbm_ensemble_sync(lbm_ensemble *e);
+
+/* Member i as a cavity handle (for lbm_melt_get, _totals, _set_hot_wall ...;
+   owned by the ensemble, not to be destroyed by the caller).  NULL if out of
+   range. */
+lbm_melt *lbm_ensemble_member(lbm_ensemble *e, int i);
+
+/* Total nodes and the launch shape in use. */
+lbm_status lbm_ensemble_info(lbm_ensemble *e, long long *n_nodes, int *grid, int *block, int *nodes_per_thread);
+
+const char *lbm_ensemble_last_error(const lbm_ensemble *e);
+void lbm_ensemble_destroy(lbm_ensemble *e);
 
 /* Library version string. */
 const char *lbm_melt_version(void);

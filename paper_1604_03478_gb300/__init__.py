@@ -7,4 +7,5 @@ small convenience wrapper (``Cavity``) and the in-tree build (``build``).
 PyTorch is used only for device buffers and streams.
 """
 from .cavity import Cavity, LbmError, default_rates  # noqa: F401
+from .ensemble import Ensemble  # noqa: F401
 from . import _abi  # noqa: F401

@@ -27,6 +27,11 @@ class lbm_melt_rates(C.Structure):
                 ("s_g5", C.c_double), ("derive_from_Ra", C.c_int)]
 
 
+class lbm_melt_case(C.Structure):
+    _fields_ = [("grid", lbm_melt_grid), ("Ra", C.c_double), ("Pr", C.c_double), ("Ste", C.c_double),
+                ("Th", C.c_double), ("Tc", C.c_double), ("Tm", C.c_double), ("rates", lbm_melt_rates)]
+
+
 class lbm_melt_info(C.Structure):
     _fields_ = [("nu", C.c_double), ("alpha", C.c_double), ("gbeta", C.c_double), ("tau_nu", C.c_double),
                 ("s_nu", C.c_double), ("s_alpha", C.c_double), ("lambda_", C.c_double), ("t0", C.c_double),
@@ -72,8 +77,20 @@ def load() -> C.CDLL:
         "lbm_melt_set_report": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
         "lbm_melt_get_report": (C.c_int, [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]),
         "lbm_melt_set_timing": (C.c_int, [vp, C.c_int]),
+        "lbm_melt_set_launch": (C.c_int, [vp, C.c_int, C.c_int]),
         "lbm_melt_kernel_time": (C.c_int, [vp, dp, C.POINTER(C.c_longlong), C.c_int]),
         "lbm_melt_last_error": (C.c_char_p, [vp]),
+        "lbm_ensemble_create": (C.c_int, [C.c_int, C.POINTER(lbm_melt_case), vp, C.POINTER(vp)]),
+        "lbm_ensemble_step": (C.c_int, [vp, C.c_longlong]),
+        "lbm_ensemble_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "lbm_ensemble_set_barrier_timeout": (C.c_int, [vp, C.c_longlong]),
+        "lbm_ensemble_inject_barrier_fault": (C.c_int, [vp, C.c_int]),
+        "lbm_ensemble_sync": (C.c_int, [vp]),
+        "lbm_ensemble_member": (vp, [vp, C.c_int]),
+        "lbm_ensemble_info": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]),
+        "lbm_ensemble_last_error": (C.c_char_p, [vp]),
+        "lbm_ensemble_destroy": (None, [vp]),
         "lbm_melt_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():

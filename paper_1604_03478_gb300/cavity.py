@@ -66,6 +66,7 @@ class Cavity:
             msg = L.lbm_melt_derive_error(C.byref(self.grid), Ra, Pr, Ste, Th, Tc, Tm, C.byref(self.rates))
             raise LbmError(st, (msg or b"").decode() or "lbm_melt_create failed")
         self._h = h
+        self._owned = True
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.face = face
@@ -73,8 +74,25 @@ class Cavity:
         self.cols_shape = (nz, nx) if face == 0 else (ny, nx)
         self.ncols = self.cols_shape[0] * self.cols_shape[1]
 
+    @classmethod
+    def _member(cls, handle, nx, ny, nz, face):
+        """View of a cavity owned by an ensemble (never destroyed here)."""
+        obj = cls.__new__(cls)
+        obj._h = C.c_void_p(handle)
+        obj._owned = False
+        obj.shape = (nz, ny, nx)
+        obj.N = nx * ny * nz
+        obj.face = face
+        obj.H = ny if face == 0 else nz
+        obj.cols_shape = (nz, nx) if face == 0 else (ny, nx)
+        obj.ncols = obj.cols_shape[0] * obj.cols_shape[1]
+        return obj
+
     # -- lifetime
     def close(self):
+        if not getattr(self, "_owned", True):
+            self._h = None
+            return
         if getattr(self, "_h", None):
             _abi.load().lbm_melt_destroy(self._h)
             self._h = None
@@ -151,6 +169,9 @@ class Cavity:
         i = _abi.lbm_melt_info()
         self._check(_abi.load().lbm_melt_get_info(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def set_launch(self, bx=0, by=0):
+        self._check(_abi.load().lbm_melt_set_launch(self._h, int(bx), int(by)))
 
     def set_timing(self, on=True):
         self._check(_abi.load().lbm_melt_set_timing(self._h, 1 if on else 0))

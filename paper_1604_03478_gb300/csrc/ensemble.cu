@@ -1,0 +1,505 @@
+// ensemble.cu -- a batch of independent cavities of uneven sizes and
+// parameters advanced by ONE persistent kernel launch (the batched form of
+// the melting step of Li, Yang & Zhang, arXiv:1604.03478, section 2).
+//
+// The launch walks a work list: per step, phase 1 covers every node of every
+// cavity in items of (block size x nodes per thread) consecutive nodes
+// (fused stream-collide, Eqs. 1-5), phase 2 every column of every cavity in
+// items of one block (front update, Eq. 6), phase 3 the same columns (phase
+// flip).  Phases are separated by a grid-wide barrier; the launch is
+// cooperative (all blocks resident) and every barrier wait is bounded: a
+// block that waits too long raises an error flag and the whole launch
+// returns, which the host reports as LBM_ETIMEOUT.  The launch (with the
+// barrier reset) is captured once in a CUDA graph and replayed.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_melt.h"
+#include "handle.h"
+#include "kernels.cuh"
+
+#define LBM_API extern "C" __attribute__((visibility("default")))
+
+namespace lbm {
+
+struct CavDesc {
+    KP p;
+    int face, cur0, inflight0, pad;
+    void *F, *G;
+    int *js[2], *nb[2];
+    double *s[2];
+    float *gpost, *thw, *thw_rd0;
+    int *status;
+};
+
+struct EnsWork {
+    int ncav;
+    int nodes_per_item;
+    const long long *item_begin;  // ncav + 1 prefix sums of node items
+    const long long *col_begin;   // ncav + 1 prefix sums of column items
+    const CavDesc *desc;
+    unsigned int *bar;            // {arrived, generation, timed out}
+    long long max_spins;
+    int skip_arrival_block;       // fault injection for tests: this block never arrives (-1: none)
+};
+
+// Grid-wide barrier with a bounded wait.  Returns false once any block has
+// given up (then every block leaves the launch).
+__device__ __forceinline__ bool grid_barrier(const EnsWork &w, unsigned int nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vb = w.bar;
+        if (vb[2]) {
+            ok = 0;
+        } else if ((int)blockIdx.x == w.skip_arrival_block) {
+            // injected fault: this block does not arrive; it waits like the
+            // others so that every block leaves through the timeout
+            long long spins = 0;
+            while (!vb[2] && ++spins <= w.max_spins) __nanosleep(256);
+            atomicExch(w.bar + 2, 1u);
+            ok = 0;
+        } else {
+            const unsigned int gen = vb[1];
+            __threadfence();
+            const unsigned int arrived = atomicAdd(w.bar, 1u) + 1u;
+            if (arrived == nblocks) {
+                atomicExch(w.bar, 0u);
+                __threadfence();
+                atomicAdd(w.bar + 1, 1u);
+            } else {
+                long long spins = 0;
+                while (vb[1] == gen) {
+                    if (vb[2] || ++spins > w.max_spins) {
+                        atomicExch(w.bar + 2, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ int find_cavity(const long long *begin, int n, long long item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copy descriptor k to shared memory if the block holds another one.
+__device__ __forceinline__ void use_cavity(const EnsWork &w, int k, CavDesc &d, int &dk) {
+    if (dk == k) return;
+    __syncthreads();
+    const int nw = (int)(sizeof(CavDesc) / 4);
+    const unsigned int *src = (const unsigned int *)(w.desc + k);
+    unsigned int *dst = (unsigned int *)&d;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) dk = k;
+    __syncthreads();
+}
+
+template <typename ST, int K>
+__global__ void __launch_bounds__(256) k_ensemble(EnsWork w, int nsteps) {
+    __shared__ __align__(16) CavDesc d;
+    __shared__ int dk;
+    if (threadIdx.x == 0) dk = -1;
+    __syncthreads();
+    const long long items1 = w.item_begin[w.ncav], items2 = w.col_begin[w.ncav];
+    for (int t = 0; t < nsteps; ++t) {
+        // phase 1: fused stream-collide of every node of every cavity
+        for (long long it = blockIdx.x; it < items1; it += gridDim.x) {
+            const int k = find_cavity(w.item_begin, w.ncav, it);
+            use_cavity(w, k, d, dk);
+            const int cur = d.cur0 ^ (t & 1), odd = d.inflight0 ^ (t & 1);
+            const float *trd = t == 0 ? d.thw_rd0 : d.thw;
+            const long long base = (it - w.item_begin[k]) * (long long)w.nodes_per_item;
+            const long long nxy = (long long)d.p.nx * d.p.ny;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const long long c = base + threadIdx.x + (long long)j * blockDim.x;
+                if (c >= d.p.N) continue;
+                const int z = (int)(c / nxy);
+                const int rem = (int)(c - z * nxy);
+                const int y = rem / d.p.nx, x = rem - y * d.p.nx;
+                ST *F = (ST *)d.F, *G = (ST *)d.G;
+                if (d.face == 0) {
+                    if (odd) odd_node<ST, 0>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
+                    else even_node<ST, 0>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, x, y, z);
+                } else {
+                    if (odd) odd_node<ST, 1>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
+                    else even_node<ST, 1>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, x, y, z);
+                }
+            }
+        }
+        if (!grid_barrier(w, gridDim.x)) return;
+        // phase 2: front update (Eq. 6) of every column
+        for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
+            const int k = find_cavity(w.col_begin, w.ncav, it);
+            use_cavity(w, k, d, dk);
+            const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
+            const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
+            if (col < d.p.ncols) {
+                const ST *F = (const ST *)d.F, *G = (const ST *)d.G;
+                if (d.face == 0)
+                    front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                        inflight, 1, d.status, col);
+                else
+                    front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                        inflight, 1, d.status, col);
+            }
+        }
+        if (!grid_barrier(w, gridDim.x)) return;
+        // phase 3: phase flip and the 3x3 liquid-count bounds
+        for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
+            const int k = find_cavity(w.col_begin, w.ncav, it);
+            use_cavity(w, k, d, dk);
+            const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
+            const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
+            if (col < d.p.ncols) {
+                ST *F = (ST *)d.F;
+                if (d.face == 0) flip_column<ST, 0>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
+                else flip_column<ST, 1>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
+            }
+        }
+        if (!grid_barrier(w, gridDim.x)) return;
+    }
+}
+
+}  // namespace lbm
+
+using lbm::CavDesc;
+using lbm::EnsWork;
+
+struct lbm_ensemble {
+    int n;
+    std::vector<lbm_melt *> cav;
+    cudaStream_t user;    // the caller's stream (ordering only)
+    cudaStream_t stream;  // own non-blocking stream: capturable, unlike the legacy default stream
+    cudaEvent_t ev_in, ev_out;
+    int precision;
+    int block, K, grid;
+    long long max_spins;
+    CavDesc *desc_dev;
+    long long *item_dev, *col_dev;
+    unsigned int *bar_dev;
+    std::vector<CavDesc> desc;
+    cudaGraphExec_t graph;
+    int graph_steps;
+    long long steps;
+    char err[512];
+};
+
+namespace {
+
+lbm_status ens_err(lbm_ensemble *e, lbm_status st, const char *fmt, ...) {
+    if (e) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(e->err, sizeof e->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define ECK(call, where)                                                                         \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return ens_err(e, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                           where, cudaGetErrorString(e_));                                       \
+    } while (0)
+
+const void *kernel_ptr(int precision, int K) {
+    if (precision == 1) {
+        if (K == 1) return (const void *)lbm::k_ensemble<__half, 1>;
+        if (K == 2) return (const void *)lbm::k_ensemble<__half, 2>;
+        return (const void *)lbm::k_ensemble<__half, 4>;
+    }
+    if (K == 1) return (const void *)lbm::k_ensemble<float, 1>;
+    if (K == 2) return (const void *)lbm::k_ensemble<float, 2>;
+    return (const void *)lbm::k_ensemble<float, 4>;
+}
+
+void fill_desc(lbm_melt *h, CavDesc &d) {
+    std::memset(&d, 0, sizeof d);
+    d.p = h->kp;
+    d.face = h->face;
+    d.cur0 = h->cur;
+    d.inflight0 = h->inflight;
+    d.F = h->F;
+    d.G = h->G;
+    for (int k = 0; k < 2; ++k) { d.js[k] = h->js[k]; d.nb[k] = h->nb[k]; d.s[k] = h->s[k]; }
+    d.gpost = h->gpost;
+    d.thw = h->thw_cur;
+    d.thw_rd0 = h->thw_pending ? h->thw_prev : h->thw_cur;
+    d.status = h->status_dev;
+}
+
+// Work-list prefix sums and the co-resident grid for the launch shape.
+lbm_status plan(lbm_ensemble *e) {
+    std::vector<long long> items(e->n + 1, 0), cols(e->n + 1, 0);
+    const long long per = (long long)e->block * e->K;
+    for (int k = 0; k < e->n; ++k) {
+        items[k + 1] = items[k] + (e->cav[k]->kp.N + per - 1) / per;
+        cols[k + 1] = cols[k] + (e->cav[k]->kp.ncols + e->block - 1) / e->block;
+    }
+    ECK(cudaMemcpyAsync(e->item_dev, items.data(), items.size() * 8, cudaMemcpyHostToDevice, e->stream), "plan");
+    ECK(cudaMemcpyAsync(e->col_dev, cols.data(), cols.size() * 8, cudaMemcpyHostToDevice, e->stream), "plan");
+    int dev = 0, sms = 0, per_sm = 0;
+    ECK(cudaGetDevice(&dev), "device");
+    ECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    ECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr(e->precision, e->K), e->block, 0),
+        "occupancy");
+    if (per_sm < 1) return ens_err(e, LBM_EINVAL, "block size %d does not fit on an SM", e->block);
+    e->grid = (int)std::min<long long>((long long)per_sm * sms, std::max(items[e->n], cols[e->n]));
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+lbm_status upload_desc(lbm_ensemble *e) {
+    for (int k = 0; k < e->n; ++k) fill_desc(e->cav[k], e->desc[k]);
+    ECK(cudaMemcpyAsync(e->desc_dev, e->desc.data(), e->desc.size() * sizeof(CavDesc), cudaMemcpyHostToDevice,
+                        e->stream), "descriptors");
+    return LBM_OK;
+}
+
+lbm_status launch(lbm_ensemble *e, int nsteps, int skip_block) {
+    EnsWork w;
+    w.ncav = e->n;
+    w.nodes_per_item = e->block * e->K;
+    w.item_begin = e->item_dev;
+    w.col_begin = e->col_dev;
+    w.desc = e->desc_dev;
+    w.bar = e->bar_dev;
+    w.max_spins = e->max_spins;
+    w.skip_arrival_block = skip_block;
+    void *args[] = {&w, &nsteps};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(e->grid);
+    cfg.blockDim = dim3(e->block);
+    cfg.stream = e->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ECK(cudaMemsetAsync(e->bar_dev, 0, 3 * sizeof(unsigned int), e->stream), "barrier reset");
+    ECK(cudaLaunchKernelExC(&cfg, kernel_ptr(e->precision, e->K), args), "ensemble launch");
+    return LBM_OK;
+}
+
+void advance_handles(lbm_ensemble *e, long long n) {
+    for (lbm_melt *h : e->cav) {
+        h->steps += n;
+        if (n & 1) { h->cur ^= 1; h->inflight ^= 1; }
+        if (n > 0) h->thw_pending = 0;
+    }
+    e->steps += n;
+}
+
+bool desc_current(lbm_ensemble *e) {
+    for (int k = 0; k < e->n; ++k) {
+        const lbm_melt *h = e->cav[k];
+        const CavDesc &d = e->desc[k];
+        if (d.cur0 != h->cur || d.inflight0 != h->inflight ||
+            d.thw_rd0 != (h->thw_pending ? h->thw_prev : h->thw_cur))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *cuda_stream, lbm_ensemble **out) {
+    if (!out || n < 1 || !cases) return LBM_EINVAL;
+    *out = nullptr;
+    lbm_ensemble *e = new (std::nothrow) lbm_ensemble();
+    if (!e) return LBM_ENOMEM;
+    e->n = n;
+    e->user = (cudaStream_t)cuda_stream;
+    e->block = 128;
+    e->K = 2;
+    e->max_spins = 1LL << 24;  // with 64 ns sleeps: about a second
+    e->graph_steps = 8;
+    e->desc.resize(n);
+    auto fail = [&](lbm_status st) {
+        for (lbm_melt *h : e->cav) lbm_melt_destroy(h);
+        cudaFree(e->desc_dev); cudaFree(e->item_dev); cudaFree(e->col_dev); cudaFree(e->bar_dev);
+        if (e->ev_in) cudaEventDestroy(e->ev_in);
+        if (e->ev_out) cudaEventDestroy(e->ev_out);
+        if (e->stream) cudaStreamDestroy(e->stream);
+        delete e;
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LBM_ECUDA);
+    // members run on the ensemble's stream, after what the caller queued so far
+    if (cudaEventRecord(e->ev_in, e->user) != cudaSuccess || cudaStreamWaitEvent(e->stream, e->ev_in, 0) != cudaSuccess)
+        return fail(LBM_ECUDA);
+    for (int k = 0; k < n; ++k) {
+        const lbm_melt_case &c = cases[k];
+        lbm_melt *h = nullptr;
+        lbm_status st = lbm_melt_create(&c.grid, c.Ra, c.Pr, c.Ste, c.Th, c.Tc, c.Tm, &c.rates, (void *)e->stream, &h);
+        if (st != LBM_OK) return fail(st);
+        e->cav.push_back(h);
+        if (k == 0) e->precision = h->precision;
+        else if (h->precision != e->precision) return fail(LBM_EINVAL);
+    }
+    if (cudaMalloc(&e->desc_dev, n * sizeof(CavDesc)) != cudaSuccess ||
+        cudaMalloc(&e->item_dev, (n + 1) * 8) != cudaSuccess || cudaMalloc(&e->col_dev, (n + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&e->bar_dev, 4 * sizeof(unsigned int)) != cudaSuccess)
+        return fail(LBM_ENOMEM);
+    if (plan(e) != LBM_OK || upload_desc(e) != LBM_OK) return fail(LBM_ECUDA);
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    *out = e;
+    return LBM_OK;
+}
+
+LBM_API void lbm_ensemble_destroy(lbm_ensemble *e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    for (lbm_melt *h : e->cav) lbm_melt_destroy(h);
+    cudaFree(e->desc_dev);
+    cudaFree(e->item_dev);
+    cudaFree(e->col_dev);
+    cudaFree(e->bar_dev);
+    cudaEventDestroy(e->ev_in);
+    cudaEventDestroy(e->ev_out);
+    cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+LBM_API const char *lbm_ensemble_last_error(const lbm_ensemble *e) { return e ? e->err : "null ensemble"; }
+
+LBM_API lbm_status lbm_ensemble_set_launch(lbm_ensemble *e, int block, int nodes_per_thread, int graph_steps) {
+    if (!e) return LBM_EINVAL;
+    if (block < 32 || block > 256 || block % 32)
+        return ens_err(e, LBM_EINVAL, "block must be a multiple of 32 in [32, 256]");
+    if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4)
+        return ens_err(e, LBM_EINVAL, "nodes_per_thread must be 1, 2 or 4");
+    if (graph_steps < 2 || (graph_steps & 1)) return ens_err(e, LBM_EINVAL, "graph_steps must be even and >= 2");
+    e->block = block;
+    e->K = nodes_per_thread;
+    e->graph_steps = graph_steps;
+    lbm_status st = plan(e);
+    if (st == LBM_OK) ECK(cudaStreamSynchronize(e->stream), "synchronize");
+    return st;
+}
+
+LBM_API lbm_status lbm_ensemble_set_barrier_timeout(lbm_ensemble *e, long long max_spins) {
+    if (!e || max_spins < 1) return LBM_EINVAL;
+    e->max_spins = max_spins;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps) {
+    if (!e || nsteps < 0) return LBM_EINVAL;
+    if (nsteps == 0) return LBM_OK;
+    // stream order: after the caller's queued work, and the caller's later
+    // work after this
+    ECK(cudaEventRecord(e->ev_in, e->user), "event");
+    ECK(cudaStreamWaitEvent(e->stream, e->ev_in, 0), "wait");
+    if (!desc_current(e)) {
+        lbm_status st = upload_desc(e);
+        if (st != LBM_OK) return st;
+    }
+    long long left = nsteps;
+    const long long G = e->graph_steps;
+    if (left >= G) {
+        if (!e->graph) {
+            cudaGraph_t g;
+            ECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal), "capture");
+            lbm_status st = launch(e, (int)G, -1);
+            cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+            if (st != LBM_OK) return st;
+            ECK(ce, "end capture");
+            ce = cudaGraphInstantiate(&e->graph, g, 0);
+            cudaGraphDestroy(g);
+            ECK(ce, "instantiate");
+        }
+        // G is even: every replay starts from the same AA phase, so the
+        // descriptors stay valid across replays
+        while (left >= G) {
+            ECK(cudaGraphLaunch(e->graph, e->stream), "graph launch");
+            left -= G;
+        }
+    }
+    if (left > 0) {
+        lbm_status st = launch(e, (int)left, -1);
+        if (st != LBM_OK) return st;
+    }
+    advance_handles(e, nsteps);
+    ECK(cudaEventRecord(e->ev_out, e->stream), "event");
+    ECK(cudaStreamWaitEvent(e->user, e->ev_out, 0), "wait");
+    return LBM_OK;
+}
+
+// Test hook: one launch of one step in which block `block` never arrives at
+// the first barrier; the bounded waits must end the launch with
+// LBM_ETIMEOUT.  The ensemble's state is not meaningful afterwards.
+LBM_API lbm_status lbm_ensemble_inject_barrier_fault(lbm_ensemble *e, int block) {
+    if (!e || block < 0 || block >= e->grid) return LBM_EINVAL;
+    if (!desc_current(e)) {
+        lbm_status st = upload_desc(e);
+        if (st != LBM_OK) return st;
+    }
+    lbm_status st = launch(e, 1, block);
+    if (st != LBM_OK) return st;
+    advance_handles(e, 1);
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_ensemble_sync(lbm_ensemble *e) {
+    if (!e) return LBM_EINVAL;
+    unsigned int bar[3] = {0, 0, 0};
+    ECK(cudaMemcpyAsync(bar, e->bar_dev, sizeof bar, cudaMemcpyDeviceToHost, e->stream), "barrier read");
+    ECK(cudaStreamSynchronize(e->stream), "synchronize");
+    if (bar[2]) return ens_err(e, LBM_ETIMEOUT, "a grid-barrier wait gave up (bounded spin exhausted)");
+    for (int k = 0; k < e->n; ++k) {
+        lbm_status st = lbm_melt_sync(e->cav[k]);
+        if (st != LBM_OK) return ens_err(e, st, "cavity %d: %s", k, lbm_melt_last_error(e->cav[k]));
+    }
+    return LBM_OK;
+}
+
+LBM_API lbm_melt *lbm_ensemble_member(lbm_ensemble *e, int i) {
+    if (!e || i < 0 || i >= e->n) return nullptr;
+    return e->cav[i];
+}
+
+LBM_API lbm_status lbm_ensemble_info(lbm_ensemble *e, long long *n_nodes, int *grid, int *block, int *nodes_per_thread) {
+    if (!e) return LBM_EINVAL;
+    long long tot = 0;
+    for (lbm_melt *h : e->cav) tot += h->kp.N;
+    if (n_nodes) *n_nodes = tot;
+    if (grid) *grid = e->grid;
+    if (block) *block = e->block;
+    if (nodes_per_thread) *nodes_per_thread = e->K;
+    return LBM_OK;
+}

@@ -1,0 +1,50 @@
+// handle.h -- internal definition of the cavity handle (opaque in the C ABI),
+// shared by the single-cavity entry points and the ensemble.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/lbm_melt.h"
+#include "lbm_core.cuh"
+
+// Lattice parameters derived from the problem statement (section 1, Eq. 7).
+struct Derived {
+    int H, P1, P2;
+    long long N, ncols;
+    double nu, alpha, gbeta, s_nu, s_alpha, lambda, t0, s0;
+    double s_e, s_eps, s_q, s_pi, s_m, s_g4, s_g5;
+};
+
+struct lbm_melt {
+    lbm::KP kp;
+    Derived d;
+    int face, precision;
+    double Ste, Th, Tc, Tm;
+    cudaStream_t stream;
+    int device;
+    void *F, *G;
+    int *js[2];
+    int *nb[2];
+    double *s[2];
+    int cur;
+    float *gpost;
+    float *thw_cur, *thw_prev;
+    int thw_pending;   // set_hot_wall happened while values were in flight
+    int *status_dev;
+    double *sum_dev;
+    double *red_part;  // scratch: per-block partials of the FP64 totals
+    int nred;          // number of partial blocks
+    double *totals_dev;  // 6 doubles
+    double *report;    // ring of report rows (7 doubles: t, totals)
+    long long report_every, report_cap, report_rows;
+    int inflight;      // last stream-collide was an even (local) step
+    long long steps;
+    size_t bytes;
+    int timing;
+    int bx, by;        // block shape of the per-node kernels (0: default)
+    std::vector<cudaEvent_t> ev;  // start/stop pairs of timed launches
+    size_t ev_used;
+    char err[512];
+};

@@ -56,13 +56,8 @@ __device__ __forceinline__ bool deep_solid(const KP &p, int a, int nbv) {
 
 // ------------------------------------------------------------- even step
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__restrict__ G,
-                                              const int *__restrict__ js, const int *__restrict__ nb,
-                                              const float *__restrict__ gpost) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
+__device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
+                                          const int *__restrict__ nb, const float *__restrict__ gpost, int x, int y, int z) {
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
@@ -84,6 +79,18 @@ __global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__re
 #pragma unroll
     for (int i = 0; i < 7; ++i) Store<ST>::st(G + opp7(i) * p.ld + c, g[i]);
 }
+
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__restrict__ G,
+                                              const int *__restrict__ js, const int *__restrict__ nb,
+                                              const float *__restrict__ gpost) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    even_node<ST, FACE>(p, F, G, js, nb, gpost, x, y, z);
+}
+
 
 // -------------------------------------------------------------- odd step
 // Bit i (1..18) of the link mask: node x - e_i is inside and liquid, i.e.
@@ -116,14 +123,10 @@ __device__ __forceinline__ float wall_value(const KP &p, int dir, float v, float
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__restrict__ G,
-                                             const int *__restrict__ js, const int *__restrict__ nb,
-                                             const float *__restrict__ gpost, const float *__restrict__ thw_rd,
-                                             const float *__restrict__ thw_wr) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
+__device__ __forceinline__ void odd_node(const KP &p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
+                                         const int *__restrict__ nb, const float *__restrict__ gpost,
+                                         const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
+                                         int y, int z) {
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
@@ -186,6 +189,19 @@ __global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__res
         Store<ST>::st(out ? Gc + p.gout[i] : Gc + opp7(i) * p.ld, out ? g[i] : wall_value<FACE>(p, i, g[i], th_wr));
     }
 }
+
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__restrict__ G,
+                                             const int *__restrict__ js, const int *__restrict__ nb,
+                                             const float *__restrict__ gpost, const float *__restrict__ thw_rd,
+                                             const float *__restrict__ thw_wr) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    odd_node<ST, FACE>(p, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+}
+
 
 // -------------------------------------------------- state gathers (natural)
 // Shifted pre-collision g of node (x,y,z).  In flight: pull from the
@@ -254,13 +270,11 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // front: g*_ghost = g^eq(T_ghost, 0) + (g*_L - g^eq(T_L, u_L)).
 // move = 0 keeps the front (used to prepare the ghost after a state upload).
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
-                                               const int *__restrict__ js, int *__restrict__ js_next,
-                                               const double *__restrict__ s, double *__restrict__ s_next,
-                                               float *__restrict__ gpost, const float *__restrict__ thw,
-                                               int inflight, int move, int *__restrict__ status) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= p.ncols) return;
+__device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
+                                           const int *__restrict__ js, int *__restrict__ js_next,
+                                           const double *__restrict__ s, double *__restrict__ s_next,
+                                           float *__restrict__ gpost, const float *__restrict__ thw, int inflight,
+                                           int move, int *__restrict__ status, int col) {
     const int P1 = p.P1, P2 = p.P2, H = p.H;
     const int pp = col % P1, q = col / P1;
     const double sc = s[col];
@@ -350,6 +364,18 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
     for (int i = 0; i < 7; ++i) gpost[(long long)i * p.ncols + col] = gh[i];
 }
 
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+                                               const int *__restrict__ js, int *__restrict__ js_next,
+                                               const double *__restrict__ s, double *__restrict__ s_next,
+                                               float *__restrict__ gpost, const float *__restrict__ thw,
+                                               int inflight, int move, int *__restrict__ status) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    front_column<ST, FACE>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col);
+}
+
+
 // ------------------------------------------------------------------ flip
 // Nodes of a column between the old and the new liquid counts changed phase.
 // Natural layout: a newly liquid node gets fh = 0 (f = f^eq(1, 0)).
@@ -364,11 +390,9 @@ __global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, c
 // over its 3x3 neighbourhood (min << 16 | max) for the interior and
 // deep-solid tests of the next stream-collide.  do_flip = 0 only records.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const int *__restrict__ js_old,
-                                              const int *__restrict__ js_new, int *__restrict__ nb_new,
-                                              int inflight, int do_flip) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= p.ncols) return;
+__device__ __forceinline__ void flip_column(const KP &p, ST *__restrict__ F, const int *__restrict__ js_old,
+                                          const int *__restrict__ js_new, int *__restrict__ nb_new, int inflight,
+                                          int do_flip, int col) {
     {
         const int pp = col % p.P1, q = col / p.P1;
         int mn = 1 << 15, mx = 0;
@@ -420,6 +444,16 @@ __global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const in
         }
     }
 }
+
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const int *__restrict__ js_old,
+                                              const int *__restrict__ js_new, int *__restrict__ nb_new,
+                                              int inflight, int do_flip) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    flip_column<ST, FACE>(p, F, js_old, js_new, nb_new, inflight, do_flip, col);
+}
+
 
 // ----------------------------------------------------- outputs and inputs
 // T and u per node (solid: Tm and 0), natural values.

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/lbm_melt.h"
+#include "handle.h"
 #include "launch.h"
 
 #define LBM_API extern "C" __attribute__((visibility("default")))
@@ -25,12 +26,7 @@ namespace {
 const double CS2T = 0.25;  // D3Q7 pseudo sound speed squared (w0 = 1/4)
 const int kRedBlocks = 608;  // partial blocks of the FP64 totals (4 per SM of a GB300)
 
-struct Derived {
-    int H, P1, P2;
-    long long N, ncols;
-    double nu, alpha, gbeta, s_nu, s_alpha, lambda, t0, s0;
-    double s_e, s_eps, s_q, s_pi, s_m, s_g4, s_g5;
-};
+
 
 // Root of lambda exp(lambda^2) erf(lambda) = Ste / sqrt(pi) (the one-phase
 // Neumann solution of conduction melting with zero subcooling, section 3.1),
@@ -115,36 +111,7 @@ lbm_status derive(const lbm_melt_grid *g, double Ra, double Pr, double Ste, doub
 
 }  // namespace
 
-struct lbm_melt {
-    KP kp;
-    Derived d;
-    int face, precision;
-    double Ste, Th, Tc, Tm;
-    cudaStream_t stream;
-    int device;
-    void *F, *G;
-    int *js[2];
-    int *nb[2];
-    double *s[2];
-    int cur;
-    float *gpost;
-    float *thw_cur, *thw_prev;
-    int thw_pending;   // set_hot_wall happened while values were in flight
-    int *status_dev;
-    double *sum_dev;
-    double *red_part;  // scratch: per-block partials of the FP64 totals
-    int nred;          // number of partial blocks
-    double *totals_dev;  // 6 doubles
-    double *report;    // ring of report rows (7 doubles: t, totals)
-    long long report_every, report_cap, report_rows;
-    int inflight;      // last stream-collide was an even (local) step
-    long long steps;
-    size_t bytes;
-    int timing;
-    std::vector<cudaEvent_t> ev;  // start/stop pairs of timed launches
-    size_t ev_used;
-    char err[512];
-};
+
 
 namespace {
 
@@ -405,7 +372,7 @@ LBM_API const char *lbm_melt_last_error(const lbm_melt *h) { return h ? h->err :
 LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
     if (!h) return LBM_EINVAL;
     if (n < 0) return set_err(h, LBM_EINVAL, "negative step count");
-    const dim3 blk = lbm::node_block(h->kp);
+    const dim3 blk = h->bx ? dim3(h->bx, h->by, 1) : lbm::node_block(h->kp);
     for (long long t = 0; t < n; ++t) {
         Bufs b = bufs(h);
         const int odd = h->inflight;
@@ -619,6 +586,16 @@ LBM_API lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info) {
     info->n_columns = d.ncols;
     info->steps = h->steps;
     info->device_bytes = h->bytes;
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_set_launch(lbm_melt *h, int bx, int by) {
+    if (!h) return LBM_EINVAL;
+    if (bx == 0 && by == 0) { h->bx = h->by = 0; return LBM_OK; }
+    if (bx < 32 || bx % 32 || by < 1 || bx * by > 128)
+        return set_err(h, LBM_EINVAL, "block shape must be a multiple of 32 along x with at most 128 threads");
+    h->bx = bx;
+    h->by = by;
     return LBM_OK;
 }
 

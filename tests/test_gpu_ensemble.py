@@ -1,0 +1,121 @@
+"""GPU tests of the batched form: one persistent launch advancing cavities of
+uneven sizes, faces and parameters must give, member by member, what the
+single-cavity path gives up to FP32 rounding (the same device functions,
+compiled inside another kernel, may contract multiply-adds differently), and
+the oracle's results within the parity tolerance; every launch shape agrees; a barrier
+whose wait runs out ends the launch with LBM_ETIMEOUT and leaves the context
+usable."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_T, TOL_LF = 1e-4, 1e-3
+
+CASES = [
+    dict(nx=20, ny=16, nz=12, face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True),
+    dict(nx=18, ny=14, nz=22, face=1, Ra=3e4, Pr=0.3, Ste=0.5, Ma=0.15, s0=2.5, derive=True),
+    dict(nx=24, ny=24, nz=24, face=0, Ra=0.0, Ste=0.1, s_nu=1.25, s_alpha=2 / 3),
+    dict(nx=33, ny=20, nz=16, face=0, Ra=5e4, Pr=0.02, Ste=0.2, Ma=0.1, s0=4.0, derive=True),
+]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1604_03478_gb300 as P
+    P.build.build()
+    return P
+
+
+def _single(P, c):
+    c = dict(c)
+    nx, ny, nz = c.pop("nx"), c.pop("ny"), c.pop("nz")
+    return P.Cavity(nx, ny, nz, **c)
+
+
+@pytest.mark.parametrize("shape", [(128, 2, 8), (64, 1, 2), (256, 4, 4)])
+def test_ensemble_matches_single_cavities(pkg, shape):
+    ens = pkg.Ensemble(CASES)
+    ens.set_launch(*shape)
+    ens.step(37)  # graph replays plus an odd remainder
+    ens.sync()
+    for k, c in enumerate(CASES):
+        single = _single(pkg, c)
+        single.step(37)
+        a = ens.member(k).get()
+        b = single.get()
+        np.testing.assert_allclose(a[0], b[0], atol=1e-5, rtol=0)
+        np.testing.assert_allclose(a[1], b[1], atol=1e-5, rtol=0)
+        np.testing.assert_allclose(a[2], b[2], atol=1e-6, rtol=0)
+        assert abs(a[3] - b[3]) <= 1e-6
+        single.close()
+    ens.close()
+
+
+def test_ensemble_against_oracle(pkg, orc):
+    ens = pkg.Ensemble(CASES)
+    ens.step(60)
+    for k in (0, 1):
+        c = dict(CASES[k])
+        o = orc.Oracle(c.pop("nx"), c.pop("ny"), c.pop("nz"), **c)
+        o.step(60)
+        Tg, ug, Sg, lfg = ens.member(k).get()
+        To, uo, So, lfo = o.get()
+        assert np.abs(Tg - To).max() <= TOL_T
+        assert np.abs(ug - uo).max() <= TOL_T
+        assert abs(lfg - lfo) <= TOL_LF
+    ens.close()
+
+
+def test_ensemble_then_member_steps(pkg):
+    """Stepping a member on its own between ensemble runs keeps the phases
+    consistent (the ensemble refreshes its descriptors)."""
+    ens = pkg.Ensemble(CASES[:2])
+    ens.step(9)
+    ens.member(1).step(3)
+    ens.step(5)
+    s0 = _single(pkg, CASES[0])
+    s1 = _single(pkg, CASES[1])
+    s0.step(14)
+    s1.step(17)
+    np.testing.assert_allclose(ens.member(0).get()[0], s0.get()[0], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(ens.member(1).get()[0], s1.get()[0], atol=1e-5, rtol=0)
+    ens.close()
+
+
+def test_barrier_timeout_is_reported(pkg):
+    """Failure detection: block 0 never arrives at the first barrier; every
+    other block's bounded wait runs out, the launch returns, the host reads
+    LBM_ETIMEOUT, and the GPU context stays usable."""
+    from paper_1604_03478_gb300 import _abi
+    ens = pkg.Ensemble(CASES[:2])
+    ens.set_barrier_timeout(20000)
+    ens.inject_barrier_fault(0)
+    with pytest.raises(pkg.LbmError) as ei:
+        ens.sync()
+    assert ei.value.status == _abi.LBM_ETIMEOUT
+    ens.close()
+    # the context still works
+    c = _single(pkg, CASES[2])
+    c.step(4)
+    T, u, S, lf = c.get()
+    assert np.isfinite(T).all()
+    c.close()
+
+
+def test_autotuner_picks_a_measured_shape(pkg, tmp_path, monkeypatch):
+    from paper_1604_03478_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    ens = pkg.Ensemble(CASES)
+    shape, rec = autotune.tune_ensemble(ens, steps=4)
+    assert shape in autotune.ENSEMBLE_SHAPES and len(rec["ms_per_step"]) == len(autotune.ENSEMBLE_SHAPES)
+    assert ens.info()["block"] == shape[0]
+    shape2, _ = autotune.tune_ensemble(ens, steps=4)  # from the cache
+    assert shape2 == shape
+    cav = _single(pkg, CASES[3])
+    cshape, crec = autotune.tune_cavity(cav, steps=4)
+    assert cshape in autotune.CAVITY_SHAPES
+    ens.close()
+    cav.close()
