@@ -20,20 +20,32 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
+_LIB_CS = os.path.join(_HERE, "liblbm_oracle_cs.so")
 
 # Non-hydrodynamic D3Q19 rates of d'Humieres et al. (2002) and inert D3Q7
 # higher-order rates; the hydrodynamic ones come from the case.
 DEFAULT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98, s_g4=1.0, s_g5=1.0)
 
 
-def build(force: bool = False) -> str:
-    """Compile ``lbm_oracle.c`` into ``liblbm_oracle.so`` (gcc, OpenMP, -O2)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
+def _compile(out, extra):
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return
+    tmp = out + ".tmp%d" % os.getpid()
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC",
-                           "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
+                           "-shared"] + extra + ["-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``lbm_oracle.c`` into ``liblbm_oracle.so`` (FP64) and
+    ``liblbm_oracle_cs.so`` (the same source in double _Complex, for
+    complex-step tangent-linear derivatives); gcc, OpenMP, -O2."""
+    if force:
+        for p in (_LIB, _LIB_CS):
+            if os.path.exists(p):
+                os.remove(p)
+    _compile(_LIB, [])
+    _compile(_LIB_CS, ["-DORC_COMPLEX"])
     return _LIB
 
 
@@ -47,28 +59,49 @@ class _Cfg(C.Structure):
 
 
 _lib = None
+_lib_cs = None
+
+
+def _declare(L):
+    dp = C.POINTER(C.c_double)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(_Cfg), C.c_char_p, C.c_int]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_step.restype = C.c_int
+    L.orc_step.argtypes = [C.c_void_p, C.c_long]
+    L.orc_get.argtypes = [C.c_void_p, dp, dp, dp, dp]
+    L.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp]
+    L.orc_set_state.argtypes = [C.c_void_p, dp, dp, dp]
+    L.orc_set_hot_wall.argtypes = [C.c_void_p, dp]
+    L.orc_info.argtypes = [C.c_void_p, dp]
+    L.orc_error.restype = C.c_char_p
+    L.orc_error.argtypes = [C.c_void_p]
+    L.orc_num_threads.restype = C.c_int
+
+
+def lib_cs() -> C.CDLL:
+    """The complex-step build (tangent-linear derivatives)."""
+    global _lib_cs
+    if _lib_cs is None:
+        build()
+        L = C.CDLL(_LIB_CS)
+        _declare(L)
+        dp = C.POINTER(C.c_double)
+        L.orc_cs_perturb.restype = C.c_int
+        L.orc_cs_perturb.argtypes = [C.c_void_p, C.c_double, dp]
+        L.orc_cs_get_s.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        _lib_cs = L
+    return _lib_cs
 
 
 def lib() -> C.CDLL:
     global _lib
     if _lib is None:
-        path = build()
-        L = C.CDLL(path)
+        build()
+        L = C.CDLL(_LIB)
+        _declare(L)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(_Cfg), C.c_char_p, C.c_int]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_step.restype = C.c_int
-        L.orc_step.argtypes = [C.c_void_p, C.c_long]
-        L.orc_get.argtypes = [C.c_void_p, dp, dp, dp, dp]
-        L.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp]
-        L.orc_set_state.argtypes = [C.c_void_p, dp, dp, dp]
-        L.orc_set_hot_wall.argtypes = [C.c_void_p, dp]
-        L.orc_info.argtypes = [C.c_void_p, dp]
-        L.orc_error.restype = C.c_char_p
-        L.orc_error.argtypes = [C.c_void_p]
-        L.orc_num_threads.restype = C.c_int
         L.orc_neumann_lambda.restype = C.c_double
         L.orc_neumann_lambda.argtypes = [C.c_double]
         L.orc_front_gradient.restype = C.c_double
@@ -187,13 +220,14 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, nz, face=0, Ra=0.0, Pr=1.0, Ste=0.1, Th=1.0, Tc=0.0, Tm=0.0,
-                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, **rates):
+                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, _lib=None, **rates):
+        self._L = _lib if _lib is not None else lib()
         r = dict(DEFAULT_RATES)
         r.update(rates)
         cfg = _Cfg(nx, ny, nz, face, Ra, Pr, Ste, Th, Tc, Tm, Ma, s0, s_nu, r["s_e"], r["s_eps"],
                    r["s_q"], r["s_pi"], r["s_m"], s_alpha, r["s_g4"], r["s_g5"], 1 if derive else 0)
         err = C.create_string_buffer(256)
-        h = lib().orc_create(C.byref(cfg), err, 256)
+        h = self._L.orc_create(C.byref(cfg), err, 256)
         if not h:
             raise OracleError(err.value.decode())
         self._h = h
@@ -206,7 +240,7 @@ class Oracle:
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -216,36 +250,56 @@ class Oracle:
             pass
 
     def step(self, n=1):
-        st = lib().orc_step(self._h, int(n))
+        st = self._L.orc_step(self._h, int(n))
         if st != 0:
-            raise OracleError("orc_step: %s" % lib().orc_error(self._h).decode())
+            raise OracleError("orc_step: %s" % self._L.orc_error(self._h).decode())
 
     def get(self):
         T = np.zeros(self.N)
         u = np.zeros(3 * self.N)
         s = np.zeros(self.ncols)
         lf = np.zeros(1)
-        lib().orc_get(self._h, _p(T), _p(u), _p(s), _p(lf))
+        self._L.orc_get(self._h, _p(T), _p(u), _p(s), _p(lf))
         return T.reshape(self.shape), u.reshape(self.shape + (3,)), s.reshape(self.cols_shape), float(lf[0])
 
     def get_state(self):
         f = np.zeros((19, self.N))
         g = np.zeros((7, self.N))
         s = np.zeros(self.ncols)
-        lib().orc_get_state(self._h, _p(f), _p(g), _p(s))
+        self._L.orc_get_state(self._h, _p(f), _p(g), _p(s))
         return f, g, s
 
     def set_state(self, f=None, g=None, s=None):
         f = None if f is None else np.ascontiguousarray(f, float).reshape(19, self.N)
         g = None if g is None else np.ascontiguousarray(g, float).reshape(7, self.N)
         s = None if s is None else np.ascontiguousarray(s, float).reshape(self.ncols)
-        lib().orc_set_state(self._h, _p(f), _p(g), _p(s))
+        self._L.orc_set_state(self._h, _p(f), _p(g), _p(s))
 
     def set_hot_wall(self, Thw):
         Thw = np.ascontiguousarray(Thw, float).reshape(self.ncols)
-        lib().orc_set_hot_wall(self._h, _p(Thw))
+        self._L.orc_set_hot_wall(self._h, _p(Thw))
 
     def info(self):
         v = np.zeros(len(INFO_KEYS))
-        lib().orc_info(self._h, _p(v))
+        self._L.orc_info(self._h, _p(v))
         return dict(zip(INFO_KEYS, v.tolist()))
+
+
+def tangent(nx, ny, nz, steps, dRa=0.0, dThw=None, h=1e-20, **kw):
+    """Directional derivative by complex step: run the oracle in complex
+    arithmetic with Ra -> Ra + i h dRa and the heated-wall field -> Th +
+    i h dThw (per column), and return (S, dS, lf, dlf): the final front
+    heights, the liquid fraction and their derivatives along the direction.
+    The phase flags are those of the unperturbed run (branches on real parts).
+    """
+    o = Oracle(nx, ny, nz, _lib=lib_cs(), **kw)
+    dT = None if dThw is None else np.ascontiguousarray(np.asarray(dThw, float).reshape(o.ncols) * h)
+    st = o._L.orc_cs_perturb(o._h, float(dRa) * h, _p(dT))
+    if st != 0:
+        raise OracleError("orc_cs_perturb failed")
+    o.step(steps)
+    re, im = np.zeros(o.ncols), np.zeros(o.ncols)
+    lre, lim = np.zeros(1), np.zeros(1)
+    o._L.orc_cs_get_s(o._h, _p(re), _p(im), _p(lre), _p(lim))
+    o.close()
+    return re.reshape(o.cols_shape), (im / h).reshape(o.cols_shape), float(lre[0]), float(lim[0] / h)

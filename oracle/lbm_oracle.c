@@ -64,6 +64,24 @@
 #include <omp.h>
 #endif
 
+/* Arithmetic type of the method.  The default build computes in double.
+   Built with -DORC_COMPLEX the same source computes in double _Complex: a
+   perturbation i*h*v of the heated-wall field or of Ra then carries the
+   directional derivative of every quantity in its imaginary part (complex-
+   step differentiation, a tangent-linear evaluation without cancellation);
+   every branch (phase flags, guarded nodes, clamps, stability check) is
+   taken on real parts, so the flags are those of the unperturbed run. */
+#ifdef ORC_COMPLEX
+#include <complex.h>
+typedef double _Complex real;
+#define RE(x) creal(x)
+#define RSQRT(x) csqrt(x)
+#else
+typedef double real;
+#define RE(x) (x)
+#define RSQRT(x) sqrt(x)
+#endif
+
 #define Q19 19
 #define Q7 7
 
@@ -96,16 +114,17 @@ typedef struct orc_sim {
     int H;           /* cavity length along the heating axis */
     int P1, P2;      /* sizes of the two in-plane (column) axes */
     long N, ncols;
-    double nu, alpha, gbeta, lambda, t0;
+    real nu, alpha, gbeta, s_nu_r, s_alpha_r;
+    double lambda, t0, Ra_im;
     double M[Q19 * Q19], Minv[Q19 * Q19], Nm[Q7 * Q7], Ninv[Q7 * Q7];
-    double S[Q19], Qr[Q7];
-    double *f, *g, *fs, *gs;     /* current (post-streaming) and post-collision */
-    double *s, *snew, *Tghost, *Thw;
-    double *Gpost;                /* ghost-node post-collision g, 7 per column */
+    real S[Q19], Qr[Q7];
+    real *f, *g, *fs, *gs;     /* current (post-streaming) and post-collision */
+    real *s, *snew, *Tghost, *Thw;
+    real *Gpost;                /* ghost-node post-collision g, 7 per column */
     int *js;                      /* number of liquid nodes per column */
     unsigned char *liq;
     long steps;
-    double q_hot, q_cold;         /* heat that entered through the isothermal walls, summed over steps */
+    real q_hot, q_cold;         /* heat that entered through the isothermal walls, summed over steps */
     int status;
     char err[256];
 } orc_sim;
@@ -219,9 +238,9 @@ static void build_N(double *Nm) {
         for (int i = 0; i < Q7; ++i) Nm[k * Q7 + i] = n_row_poly(k, TX[i], TY[i], TZ[i]);
 }
 
-static void matvec(int n, const double *A, const double *x, double *y) {
+static void matvec(int n, const double *A, const real *x, real *y) {
     for (int r = 0; r < n; ++r) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int c = 0; c < n; ++c) acc += A[r * n + c] * x[c];
         y[r] = acc;
     }
@@ -231,30 +250,30 @@ static void matvec(int n, const double *A, const double *x, double *y) {
 
 /* Incompressible D3Q19 BGK equilibrium with rho0 = 1 (the textbook second-order
    polynomial); its moments M f^eq are the m^eq of Eq. 2. */
-static void feq19(double rho, const double *u, double *out) {
-    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+static void feq19(real rho, const real *u, real *out) {
+    real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     for (int i = 0; i < Q19; ++i) {
-        double eu = EX[i] * u[0] + EY[i] * u[1] + EZ[i] * u[2];
+        real eu = EX[i] * u[0] + EY[i] * u[1] + EZ[i] * u[2];
         out[i] = w19(i) * (rho + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
     }
 }
 
 /* D3Q7 equilibrium, linear in u: g^eq_i = w_i T (1 + e_i.u / cs2T). */
-static void geq7(double T, const double *u, double *out) {
+static void geq7(real T, const real *u, real *out) {
     for (int i = 0; i < Q7; ++i) {
-        double eu = TX[i] * u[0] + TY[i] * u[1] + TZ[i] * u[2];
+        real eu = TX[i] * u[0] + TY[i] * u[1] + TZ[i] * u[2];
         out[i] = w7(i) * T * (1.0 + eu / CS2T);
     }
 }
 
 /* Guo's discrete forcing term F~_i = w_i [3 (e_i - u).F + 9 (e_i.u)(e_i.F)]
    (the F_i of Eq. 1 before the (I - S/2) moment-space factor). */
-static void guo19(const double *u, const double *F, double *out) {
+static void guo19(const real *u, const real *F, real *out) {
     for (int i = 0; i < Q19; ++i) {
-        double e[3] = {EX[i], EY[i], EZ[i]};
-        double emuF = (e[0] - u[0]) * F[0] + (e[1] - u[1]) * F[1] + (e[2] - u[2]) * F[2];
-        double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
-        double eF = e[0] * F[0] + e[1] * F[1] + e[2] * F[2];
+        real e[3] = {EX[i], EY[i], EZ[i]};
+        real emuF = (e[0] - u[0]) * F[0] + (e[1] - u[1]) * F[1] + (e[2] - u[2]) * F[2];
+        real eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        real eF = e[0] * F[0] + e[1] * F[1] + e[2] * F[2];
         out[i] = w19(i) * (3.0 * emuF + 9.0 * eu * eF);
     }
 }
@@ -263,11 +282,11 @@ static void guo19(const double *u, const double *F, double *out) {
 
 /* Eqs. 1-2 with forcing: m = M f; u = (sum f e + F/2)/rho0;
    m* = m - S (m - m^eq) + (I - S/2) M F~;  f* = M^-1 m*.  Writes u too. */
-static void collide_f(const double *M, const double *Minv, const double *S,
-                      const double *f, const double *F, double *fout, double *u) {
-    double m[Q19], meq[Q19], mF[Q19], fe[Q19], Fi[Q19], ms[Q19];
+static void collide_f(const double *M, const double *Minv, const real *S,
+                      const real *f, const real *F, real *fout, real *u) {
+    real m[Q19], meq[Q19], mF[Q19], fe[Q19], Fi[Q19], ms[Q19];
     matvec(Q19, M, f, m);
-    double rho = m[0];
+    real rho = m[0];
     u[0] = m[3] + 0.5 * F[0];
     u[1] = m[5] + 0.5 * F[1];
     u[2] = m[7] + 0.5 * F[2];
@@ -280,10 +299,10 @@ static void collide_f(const double *M, const double *Minv, const double *S,
 }
 
 /* Eq. 4: n = N g; n* = n - Q (n - n^eq); g* = N^-1 n*. */
-static void collide_g(const double *Nm, const double *Ninv, const double *Qr,
-                      const double *g, const double *u, double *gout) {
-    double n[Q7], neq[Q7], ge[Q7], ns[Q7];
-    double T = 0.0;
+static void collide_g(const double *Nm, const double *Ninv, const real *Qr,
+                      const real *g, const real *u, real *gout) {
+    real n[Q7], neq[Q7], ge[Q7], ns[Q7];
+    real T = 0.0;
     for (int i = 0; i < Q7; ++i) T += g[i];
     matvec(Q7, Nm, g, n);
     geq7(T, u, ge);
@@ -309,8 +328,8 @@ double orc_neumann_lambda(double Ste) {
 }
 
 /* Highest node k (centre k + 1/2) at least half a cell below s, or -1. */
-static int guarded_node(double s, int n) {
-    int k = (int)floor(s - 1.0);
+static int guarded_node(real s, int n) {
+    int k = (int)floor(RE(s) - 1.0);
     if (k > n - 1) k = n - 1;
     return k < 0 ? -1 : k;
 }
@@ -320,10 +339,10 @@ static int guarded_node(double s, int n) {
    temperature at a = 0.  Quadratic through (y_{k-1}, T_{k-1}), (y_k, T_k),
    (s, Tm), with (0, Tw) standing in for node k-1 when k = 0; linear through
    (0, Tw) and (s, Tm) when no node is at least half a cell below s. */
-double orc_front_gradient(const double *Tcol, int n, double s, double Tw, double Tm) {
+static real front_gradient(const real *Tcol, int n, real s, real Tw, real Tm) {
     int k = guarded_node(s, n);
     if (k < 0) return (Tm - Tw) / s;
-    double x0, y0, x1 = k + 0.5, y1 = Tcol[k], x2 = s, y2 = Tm;
+    real x0, y0, x1 = k + 0.5, y1 = Tcol[k], x2 = s, y2 = Tm;
     if (k >= 1) { x0 = k - 0.5; y0 = Tcol[k - 1]; }
     else        { x0 = 0.0;     y0 = Tw; }
     return y0 * (x2 - x1) / ((x0 - x1) * (x0 - x2))
@@ -332,20 +351,20 @@ double orc_front_gradient(const double *Tcol, int n, double s, double Tw, double
 }
 
 /* Number of liquid nodes in a column: node j is liquid iff j + 1/2 < s. */
-static int n_liquid(double s, int n) {
+static int n_liquid(real s, int n) {
     int c = 0;
     for (int j = 0; j < n; ++j)
-        if (j + 0.5 < s) ++c;
+        if (j + 0.5 < RE(s)) ++c;
     return c;
 }
 
 /* Ghost temperature of the first solid node of a column: the line through the
    guarded liquid node (or the heated wall) and (s, Tm), evaluated at that
    node's centre.  Returns Tm when the column has no solid node. */
-double orc_ghost_T(const double *Tcol, int n, double s, double Tw, double Tm) {
+static real ghost_T(const real *Tcol, int n, real s, real Tw, real Tm) {
     int js = n_liquid(s, n);
     if (js >= n) return Tm;
-    double yg = js + 0.5;
+    real yg = js + 0.5;
     int k = guarded_node(s, n);
     if (k < 0) return Tm + (Tm - Tw) * (yg - s) / s;
     return Tm + (Tm - Tcol[k]) * (yg - s) / (s - (k + 0.5));
@@ -384,13 +403,13 @@ static int inside(const orc_sim *S, int x, int y, int z) {
     return x >= 0 && y >= 0 && z >= 0 && x < S->cfg.nx && y < S->cfg.ny && z < S->cfg.nz;
 }
 
-static double cell_T(const orc_sim *S, long c) {
-    double T = 0.0;
+static real cell_T(const orc_sim *S, long c) {
+    real T = 0.0;
     for (int i = 0; i < Q7; ++i) T += S->g[c * Q7 + i];
     return T;
 }
 
-static void column_T(const orc_sim *S, long col, double *Tcol) {
+static void column_T(const orc_sim *S, long col, real *Tcol) {
     for (int j = 0; j < S->H; ++j) Tcol[j] = cell_T(S, column_cell(S, col, j));
 }
 
@@ -399,13 +418,13 @@ static void refresh_flags(orc_sim *S) {
     for (long c = 0; c < S->N; ++c) {
         int x, y, z;
         coords(S, c, &x, &y, &z);
-        S->liq[c] = (axial_of(S, x, y, z) + 0.5 < S->s[column_of(S, x, y, z)]) ? 1 : 0;
+        S->liq[c] = (axial_of(S, x, y, z) + 0.5 < RE(S->s[column_of(S, x, y, z)])) ? 1 : 0;
     }
 }
 
 /* Force-shifted velocity of a liquid node, u = sum f e + F/2 (rho0 = 1). */
-static void cell_u(const orc_sim *S, long c, double T, double *u) {
-    const double *f = S->f + c * Q19;
+static void cell_u(const orc_sim *S, long c, real T, real *u) {
+    const real *f = S->f + c * Q19;
     u[0] = u[1] = u[2] = 0.0;
     for (int i = 0; i < Q19; ++i) {
         u[0] += f[i] * EX[i];
@@ -420,18 +439,18 @@ static void cell_u(const orc_sim *S, long c, double T, double *u) {
    (g*_L - g^eq(T_L, u_L)), L the liquid node below the ghost (none: the
    equilibrium alone). */
 static void refresh_ghosts(orc_sim *S) {
-    double *Tcol = (double *)malloc(sizeof(double) * S->H);
-    double zero[3] = {0.0, 0.0, 0.0};
+    real *Tcol = (real *)malloc(sizeof(real) * S->H);
+    real zero[3] = {0.0, 0.0, 0.0};
     for (long col = 0; col < S->ncols; ++col) {
         column_T(S, col, Tcol);
-        double Tg = orc_ghost_T(Tcol, S->H, S->s[col], S->Thw[col], S->cfg.Tm);
+        real Tg = ghost_T(Tcol, S->H, S->s[col], S->Thw[col], S->cfg.Tm);
         S->Tghost[col] = Tg;
-        double *gp = S->Gpost + col * Q7;
+        real *gp = S->Gpost + col * Q7;
         geq7(Tg, zero, gp);
         int js = S->js[col];
         if (js >= 1 && js < S->H) {
             long L = column_cell(S, col, js - 1);
-            double uL[3], gsL[Q7], geL[Q7];
+            real uL[3], gsL[Q7], geL[Q7];
             cell_u(S, L, Tcol[js - 1], uL);
             collide_g(S->Nm, S->Ninv, S->Qr, S->g + L * Q7, uL, gsL);
             geq7(Tcol[js - 1], uL, geL);
@@ -462,27 +481,34 @@ static int derive(orc_sim *S) {
     if (c->Tc > c->Tm) return set_err(S, "Tc must not exceed Tm");
     if (!(c->Ste >= 0.0)) return set_err(S, "Ste must be >= 0");
     if (!(c->Ra >= 0.0)) return set_err(S, "Ra must be >= 0");
+    /* Ra carries the complex-step perturbation in the complex build */
+    real Ra = c->Ra;
+#ifdef ORC_COMPLEX
+    Ra += I * S->Ra_im;
+#endif
     if (c->derive) {
         if (!(c->Ra > 0.0) || !(c->Pr > 0.0) || !(c->Ma > 0.0)) return set_err(S, "derive needs Ra, Pr, Ma > 0");
-        double U0 = c->Ma / sqrt(3.0);
-        S->nu = U0 * S->H * sqrt(c->Pr / c->Ra);
+        real U0 = c->Ma / sqrt(3.0);
+        S->nu = U0 * S->H * RSQRT(c->Pr / Ra);
         S->alpha = S->nu / c->Pr;
-        c->s_nu = 1.0 / (3.0 * S->nu + 0.5);
-        c->s_alpha = 1.0 / (S->alpha / CS2T + 0.5);
+        S->s_nu_r = 1.0 / (3.0 * S->nu + 0.5);
+        S->s_alpha_r = 1.0 / (S->alpha / CS2T + 0.5);
     } else {
+        S->s_nu_r = c->s_nu;
+        S->s_alpha_r = c->s_alpha;
         S->nu = (1.0 / c->s_nu - 0.5) / 3.0;
         S->alpha = CS2T * (1.0 / c->s_alpha - 0.5);
     }
-    S->gbeta = c->Ra > 0.0 ? c->Ra * S->nu * S->alpha / ((c->Th - c->Tm) * pow((double)S->H, 3)) : 0.0;
+    S->gbeta = c->Ra > 0.0 ? Ra * S->nu * S->alpha / ((c->Th - c->Tm) * pow((double)S->H, 3)) : 0.0;
     double s0 = c->s0 > 0.0 ? c->s0 : 1.0;
     if (s0 < 0.5 || s0 > S->H) return set_err(S, "s0 outside [0.5, H]");
     c->s0 = s0;
     /* D3Q19 rates by moment row: conserved rows 0, 3, 5, 7 are inert (1). */
-    double sr[Q19] = {1.0, c->s_e, c->s_eps, 1.0, c->s_q, 1.0, c->s_q, 1.0, c->s_q,
-                      c->s_nu, c->s_pi, c->s_nu, c->s_pi, c->s_nu, c->s_nu, c->s_nu,
+    real sr[Q19] = {1.0, c->s_e, c->s_eps, 1.0, c->s_q, 1.0, c->s_q, 1.0, c->s_q,
+                      S->s_nu_r, c->s_pi, S->s_nu_r, c->s_pi, S->s_nu_r, S->s_nu_r, S->s_nu_r,
                       c->s_m, c->s_m, c->s_m};
     memcpy(S->S, sr, sizeof sr);
-    double qr[Q7] = {1.0, c->s_alpha, c->s_alpha, c->s_alpha, c->s_g4, c->s_g5, c->s_g5};
+    real qr[Q7] = {1.0, S->s_alpha_r, S->s_alpha_r, S->s_alpha_r, c->s_g4, c->s_g5, c->s_g5};
     memcpy(S->Qr, qr, sizeof qr);
     return ORC_OK;
 }
@@ -502,16 +528,16 @@ orc_sim *orc_create(const orc_cfg *cfg, char *err, int errlen) {
     invert(Q7, S->Nm, S->Ninv);
     S->N = (long)cfg->nx * cfg->ny * cfg->nz;
     S->ncols = (long)S->P1 * S->P2;
-    S->f = (double *)calloc((size_t)S->N * Q19, sizeof(double));
-    S->fs = (double *)calloc((size_t)S->N * Q19, sizeof(double));
-    S->g = (double *)calloc((size_t)S->N * Q7, sizeof(double));
-    S->gs = (double *)calloc((size_t)S->N * Q7, sizeof(double));
-    S->s = (double *)calloc(S->ncols, sizeof(double));
-    S->snew = (double *)calloc(S->ncols, sizeof(double));
-    S->Tghost = (double *)calloc(S->ncols, sizeof(double));
-    S->Thw = (double *)calloc(S->ncols, sizeof(double));
+    S->f = (real *)calloc((size_t)S->N * Q19, sizeof(real));
+    S->fs = (real *)calloc((size_t)S->N * Q19, sizeof(real));
+    S->g = (real *)calloc((size_t)S->N * Q7, sizeof(real));
+    S->gs = (real *)calloc((size_t)S->N * Q7, sizeof(real));
+    S->s = (real *)calloc(S->ncols, sizeof(real));
+    S->snew = (real *)calloc(S->ncols, sizeof(real));
+    S->Tghost = (real *)calloc(S->ncols, sizeof(real));
+    S->Thw = (real *)calloc(S->ncols, sizeof(real));
     S->js = (int *)calloc(S->ncols, sizeof(int));
-    S->Gpost = (double *)calloc((size_t)S->ncols * Q7, sizeof(double));
+    S->Gpost = (real *)calloc((size_t)S->ncols * Q7, sizeof(real));
     S->liq = (unsigned char *)calloc(S->N, 1);
     if (!S->f || !S->fs || !S->g || !S->gs || !S->s || !S->snew || !S->Tghost || !S->Thw || !S->js ||
         !S->Gpost || !S->liq) {
@@ -526,20 +552,22 @@ orc_sim *orc_create(const orc_cfg *cfg, char *err, int errlen) {
        t0 = s0^2 / (4 lambda^2 alpha); at rest, rho = 1.  With Ste = 0 (front
        held fixed) the liquid starts at Tm.  Solid at Tm. */
     S->lambda = orc_neumann_lambda(c->Ste);
-    S->t0 = c->Ste > 0.0 ? c->s0 * c->s0 / (4.0 * S->lambda * S->lambda * S->alpha) : 0.0;
+    S->t0 = c->Ste > 0.0 ? c->s0 * c->s0 / (4.0 * S->lambda * S->lambda * RE(S->alpha)) : 0.0;
     for (long col = 0; col < S->ncols; ++col) {
         S->s[col] = c->s0;
         S->Thw[col] = c->Th;
     }
     refresh_flags(S);
-    double zero[3] = {0.0, 0.0, 0.0};
+    real zero[3] = {0.0, 0.0, 0.0};
     for (long cc = 0; cc < S->N; ++cc) {
         int x, y, z;
         coords(S, cc, &x, &y, &z);
-        double a = axial_of(S, x, y, z) + 0.5, T = c->Tm;
+        double a = axial_of(S, x, y, z) + 0.5;
+        real T = c->Tm;
         if (S->liq[cc]) {
+            /* alpha t0 = s0^2 / (4 lambda^2) does not depend on alpha */
             if (c->Ste > 0.0)
-                T = c->Th - (c->Th - c->Tm) * erf(a / (2.0 * sqrt(S->alpha * S->t0))) / erf(S->lambda);
+                T = c->Th - (c->Th - c->Tm) * erf(a / (2.0 * sqrt(RE(S->alpha) * S->t0))) / erf(S->lambda);
             feq19(1.0, zero, S->f + cc * Q19);
         }
         geq7(T, zero, S->g + cc * Q7);
@@ -558,26 +586,26 @@ void orc_destroy(orc_sim *S) {
 /* ---------------------------------------------------------------- stepping */
 
 static void collide_all(orc_sim *S) {
-    const double Tm = S->cfg.Tm;
+    const real Tm = S->cfg.Tm;
     #pragma omp parallel for schedule(static)
     for (long c = 0; c < S->N; ++c) {
         int x, y, z;
         coords(S, c, &x, &y, &z);
         if (S->liq[c]) {
-            const double *g = S->g + c * Q7;
-            double T = 0.0;
+            const real *g = S->g + c * Q7;
+            real T = 0.0;
             for (int i = 0; i < Q7; ++i) T += g[i];
             /* Boussinesq buoyancy, gravity along -z, reference temperature Tm. */
-            double F[3] = {0.0, 0.0, S->gbeta * (T - Tm)};
-            double u[3];
+            real F[3] = {0.0, 0.0, S->gbeta * (T - Tm)};
+            real u[3];
             collide_f(S->M, S->Minv, S->S, S->f + c * Q19, F, S->fs + c * Q19, u);
             collide_g(S->Nm, S->Ninv, S->Qr, g, u, S->gs + c * Q7);
         } else {
             long col = column_of(S, x, y, z);
             int j = axial_of(S, x, y, z);
-            double zero[3] = {0.0, 0.0, 0.0};
+            real zero[3] = {0.0, 0.0, 0.0};
             if (j == S->js[col]) /* ghost node */
-                memcpy(S->gs + c * Q7, S->Gpost + col * Q7, sizeof(double) * Q7);
+                memcpy(S->gs + c * Q7, S->Gpost + col * Q7, sizeof(real) * Q7);
             else
                 geq7(Tm, zero, S->gs + c * Q7);
             for (int i = 0; i < Q19; ++i) S->fs[c * Q19 + i] = 0.0;
@@ -603,7 +631,7 @@ static void stream_all(orc_sim *S) {
     for (long c = 0; c < S->N; ++c) {
         int x, y, z;
         coords(S, c, &x, &y, &z);
-        double *fn = S->f + c * Q19;
+        real *fn = S->f + c * Q19;
         if (S->liq[c]) {
             for (int i = 0; i < Q19; ++i) {
                 int ux = x - EX[i], uy = y - EY[i], uz = z - EZ[i];
@@ -615,7 +643,7 @@ static void stream_all(orc_sim *S) {
         } else {
             for (int i = 0; i < Q19; ++i) fn[i] = 0.0;
         }
-        double *gn = S->g + c * Q7;
+        real *gn = S->g + c * Q7;
         long col = column_of(S, x, y, z);
         for (int i = 0; i < Q7; ++i) {
             int kind = wall_kind7(S, x, y, z, i);
@@ -624,7 +652,7 @@ static void stream_all(orc_sim *S) {
             } else if (kind == 3) { /* adiabatic wall: bounce-back */
                 gn[i] = S->gs[c * Q7 + opp7(i)];
             } else { /* isothermal wall: anti-bounce-back -g*_opp + 2 w_i Tw */
-                double Tw = kind == 1 ? S->Thw[col] : S->cfg.Tc;
+                real Tw = kind == 1 ? S->Thw[col] : S->cfg.Tc;
                 gn[i] = -S->gs[c * Q7 + opp7(i)] + 2.0 * w7(i) * Tw;
             }
         }
@@ -639,7 +667,7 @@ static void stream_all(orc_sim *S) {
             for (int i = 0; i < Q7; ++i) {
                 int kind = wall_kind7(S, x, y, z, i);
                 if (kind == 1 || kind == 2) {
-                    double in = S->g[c * Q7 + i], out = S->gs[c * Q7 + opp7(i)];
+                    real in = S->g[c * Q7 + i], out = S->gs[c * Q7 + opp7(i)];
                     if (kind == 1) S->q_hot += in - out; else S->q_cold += in - out;
                 }
             }
@@ -656,38 +684,38 @@ static int front_update(orc_sim *S) {
     const orc_cfg *c = &S->cfg;
     int P1 = S->P1, P2 = S->P2, bad = 0;
     /* Ste = 0 (infinite latent heat) holds the front in place. */
-    double coef = c->Ste > 0.0 ? S->alpha * c->Ste / (c->Th - c->Tm) : 0.0;
-    double *Tcol = (double *)malloc(sizeof(double) * S->H);
+    real coef = c->Ste > 0.0 ? S->alpha * c->Ste / (c->Th - c->Tm) : 0.0;
+    real *Tcol = (real *)malloc(sizeof(real) * S->H);
     for (long col = 0; col < S->ncols; ++col) {
         int p = (int)(col % P1), q = (int)(col / P1);
-        double sp_hi = S->s[(long)q * P1 + (p + 1 < P1 ? p + 1 : p)];
-        double sp_lo = S->s[(long)q * P1 + (p - 1 >= 0 ? p - 1 : p)];
-        double sq_hi = S->s[(long)(q + 1 < P2 ? q + 1 : q) * P1 + p];
-        double sq_lo = S->s[(long)(q - 1 >= 0 ? q - 1 : q) * P1 + p];
-        double sp = 0.5 * (sp_hi - sp_lo), sq = 0.5 * (sq_hi - sq_lo);
+        real sp_hi = S->s[(long)q * P1 + (p + 1 < P1 ? p + 1 : p)];
+        real sp_lo = S->s[(long)q * P1 + (p - 1 >= 0 ? p - 1 : p)];
+        real sq_hi = S->s[(long)(q + 1 < P2 ? q + 1 : q) * P1 + p];
+        real sq_lo = S->s[(long)(q - 1 >= 0 ? q - 1 : q) * P1 + p];
+        real sp = 0.5 * (sp_hi - sp_lo), sq = 0.5 * (sq_hi - sq_lo);
         column_T(S, col, Tcol);
-        double G = orc_front_gradient(Tcol, S->H, S->s[col], S->Thw[col], c->Tm);
-        double v = coef * (1.0 + sp * sp + sq * sq) * (-G);
-        if (!(fabs(v) <= 0.5)) bad = 1;
-        double sn = S->s[col] + v;
-        if (sn < 0.5) sn = 0.5;
-        if (sn > S->H) sn = S->H;
+        real G = front_gradient(Tcol, S->H, S->s[col], S->Thw[col], c->Tm);
+        real v = coef * (1.0 + sp * sp + sq * sq) * (-G);
+        if (!(fabs(RE(v)) <= 0.5)) bad = 1;
+        real sn = S->s[col] + v;
+        if (RE(sn) < 0.5) sn = 0.5;
+        if (RE(sn) > S->H) sn = S->H;
         S->snew[col] = sn;
     }
     free(Tcol);
-    double *t = S->s; S->s = S->snew; S->snew = t;
+    real *t = S->s; S->s = S->snew; S->snew = t;
     return bad ? ORC_EUNSTABLE : ORC_OK;
 }
 
 /* Phase flip: a node the front passed becomes liquid with f = f^eq(1, 0); a
    node the front receded over becomes solid (its f is dropped).  g is kept. */
 static void flip(orc_sim *S) {
-    double zero[3] = {0.0, 0.0, 0.0}, fe[Q19];
+    real zero[3] = {0.0, 0.0, 0.0}, fe[Q19];
     feq19(1.0, zero, fe);
     for (long c = 0; c < S->N; ++c) {
         int x, y, z;
         coords(S, c, &x, &y, &z);
-        unsigned char now = (axial_of(S, x, y, z) + 0.5 < S->s[column_of(S, x, y, z)]) ? 1 : 0;
+        unsigned char now = (axial_of(S, x, y, z) + 0.5 < RE(S->s[column_of(S, x, y, z)])) ? 1 : 0;
         if (now && !S->liq[c]) memcpy(S->f + c * Q19, fe, sizeof fe);
         if (!now && S->liq[c]) memset(S->f + c * Q19, 0, sizeof fe);
         S->liq[c] = now;
@@ -720,10 +748,10 @@ int orc_step(orc_sim *S, long nsteps) {
    T = Tm, u = 0), the front heights, and the liquid fraction sum(s)/(H ncols). */
 void orc_get(const orc_sim *S, double *T, double *u, double *s, double *lf) {
     for (long c = 0; c < S->N; ++c) {
-        double Tc = S->cfg.Tm, uc[3] = {0.0, 0.0, 0.0};
+        real Tc = S->cfg.Tm, uc[3] = {0.0, 0.0, 0.0};
         if (S->liq[c]) {
             Tc = cell_T(S, c);
-            const double *f = S->f + c * Q19;
+            const real *f = S->f + c * Q19;
             for (int i = 0; i < Q19; ++i) {
                 uc[0] += f[i] * EX[i];
                 uc[1] += f[i] * EY[i];
@@ -731,14 +759,15 @@ void orc_get(const orc_sim *S, double *T, double *u, double *s, double *lf) {
             }
             uc[2] += 0.5 * S->gbeta * (Tc - S->cfg.Tm);
         }
-        if (T) T[c] = Tc;
-        if (u) { u[3 * c] = uc[0]; u[3 * c + 1] = uc[1]; u[3 * c + 2] = uc[2]; }
+        if (T) T[c] = RE(Tc);
+        if (u) { u[3 * c] = RE(uc[0]); u[3 * c + 1] = RE(uc[1]); u[3 * c + 2] = RE(uc[2]); }
     }
-    if (s) memcpy(s, S->s, sizeof(double) * S->ncols);
+    if (s)
+        for (long col = 0; col < S->ncols; ++col) s[col] = RE(S->s[col]);
     if (lf) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (long col = 0; col < S->ncols; ++col) acc += S->s[col];
-        *lf = acc / ((double)S->H * (double)S->ncols);
+        *lf = RE(acc / ((double)S->H * (double)S->ncols));
     }
 }
 
@@ -746,11 +775,12 @@ void orc_get(const orc_sim *S, double *T, double *u, double *s, double *lf) {
 void orc_get_state(const orc_sim *S, double *f, double *g, double *s) {
     if (f)
         for (long c = 0; c < S->N; ++c)
-            for (int i = 0; i < Q19; ++i) f[(long)i * S->N + c] = S->f[c * Q19 + i];
+            for (int i = 0; i < Q19; ++i) f[(long)i * S->N + c] = RE(S->f[c * Q19 + i]);
     if (g)
         for (long c = 0; c < S->N; ++c)
-            for (int i = 0; i < Q7; ++i) g[(long)i * S->N + c] = S->g[c * Q7 + i];
-    if (s) memcpy(s, S->s, sizeof(double) * S->ncols);
+            for (int i = 0; i < Q7; ++i) g[(long)i * S->N + c] = RE(S->g[c * Q7 + i]);
+    if (s)
+        for (long col = 0; col < S->ncols; ++col) s[col] = RE(S->s[col]);
 }
 
 /* Replace the state; flags and ghost nodes are recomputed from s and g.  A
@@ -758,9 +788,10 @@ void orc_get_state(const orc_sim *S, double *f, double *g, double *s) {
    values are reset every step), so solid nodes are stored at rest: f = 0,
    g = g^eq(Tm, 0). */
 void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s) {
-    if (s) memcpy(S->s, s, sizeof(double) * S->ncols);
+    if (s)
+        for (long col = 0; col < S->ncols; ++col) S->s[col] = s[col];
     refresh_flags(S);
-    double zero[3] = {0.0, 0.0, 0.0}, gm[Q7];
+    real zero[3] = {0.0, 0.0, 0.0}, gm[Q7];
     geq7(S->cfg.Tm, zero, gm);
     if (f)
         for (long c = 0; c < S->N; ++c)
@@ -775,7 +806,7 @@ void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s
    It takes effect at the next step's streaming; the ghost nodes of the
    current state were prepared with the field of the step that produced it. */
 void orc_set_hot_wall(orc_sim *S, const double *Thw) {
-    memcpy(S->Thw, Thw, sizeof(double) * S->ncols);
+    for (long col = 0; col < S->ncols; ++col) S->Thw[col] = Thw[col];
 }
 
 /* info[0..]: nu, alpha, gbeta, lambda, t0, s_nu, s_alpha, H, steps, q_hot,
@@ -785,12 +816,12 @@ void orc_info(const orc_sim *S, double *info) {
     double mass = 0.0, nl = 0.0, eT = 0.0;
     for (long c = 0; c < S->N; ++c) {
         if (!S->liq[c]) continue;
-        for (int i = 0; i < Q19; ++i) mass += S->f[c * Q19 + i];
-        eT += cell_T(S, c);
+        for (int i = 0; i < Q19; ++i) mass += RE(S->f[c * Q19 + i]);
+        eT += RE(cell_T(S, c));
         nl += 1.0;
     }
-    double v[14] = {S->nu, S->alpha, S->gbeta, S->lambda, S->t0, S->cfg.s_nu, S->cfg.s_alpha,
-                    (double)S->H, (double)S->steps, S->q_hot, S->q_cold, mass, nl, eT};
+    double v[14] = {RE(S->nu), RE(S->alpha), RE(S->gbeta), S->lambda, S->t0, RE(S->s_nu_r), RE(S->s_alpha_r),
+                    (double)S->H, (double)S->steps, RE(S->q_hot), RE(S->q_cold), mass, nl, eT};
     memcpy(info, v, sizeof v);
 }
 
@@ -805,21 +836,22 @@ int orc_num_threads(void) {
 }
 
 /* ----------------------------------------------------- unit-level exports */
+#ifndef ORC_COMPLEX
 
-void orc_lattice19(int *ex, int *ey, int *ez, double *w, int *opp) {
+void orc_lattice19(int *ex, int *ey, int *ez, real *w, int *opp) {
     for (int i = 0; i < Q19; ++i) {
         ex[i] = EX[i]; ey[i] = EY[i]; ez[i] = EZ[i]; w[i] = w19(i); opp[i] = opp19(i);
     }
 }
 
-void orc_lattice7(int *ex, int *ey, int *ez, double *w, int *opp) {
+void orc_lattice7(int *ex, int *ey, int *ez, real *w, int *opp) {
     for (int i = 0; i < Q7; ++i) {
         ex[i] = TX[i]; ey[i] = TY[i]; ez[i] = TZ[i]; w[i] = w7(i); opp[i] = opp7(i);
     }
 }
 
-void orc_matrices(double *M, double *Minv, double *Nm, double *Ninv) {
-    double a[Q19 * Q19], b[Q7 * Q7];
+void orc_matrices(real *M, real *Minv, real *Nm, real *Ninv) {
+    real a[Q19 * Q19], b[Q7 * Q7];
     build_M(a);
     build_N(b);
     if (M) memcpy(M, a, sizeof a);
@@ -828,22 +860,60 @@ void orc_matrices(double *M, double *Minv, double *Nm, double *Ninv) {
     if (Ninv) invert(Q7, b, Ninv);
 }
 
-void orc_feq19(double rho, const double *u, double *out) { feq19(rho, u, out); }
-void orc_geq7(double T, const double *u, double *out) { geq7(T, u, out); }
-void orc_guo19(const double *u, const double *F, double *out) { guo19(u, F, out); }
+void orc_feq19(real rho, const real *u, real *out) { feq19(rho, u, out); }
+void orc_geq7(real T, const real *u, real *out) { geq7(T, u, out); }
+void orc_guo19(const real *u, const real *F, real *out) { guo19(u, F, out); }
 
 /* One D3Q19 collision with the given 19 rates and force; u receives the
    force-shifted velocity. */
-void orc_collide_f(const double *f, const double *S19, const double *F, double *fout, double *u) {
-    double M[Q19 * Q19], Minv[Q19 * Q19];
+void orc_collide_f(const real *f, const real *S19, const real *F, real *fout, real *u) {
+    real M[Q19 * Q19], Minv[Q19 * Q19];
     build_M(M);
     invert(Q19, M, Minv);
     collide_f(M, Minv, S19, f, F, fout, u);
 }
 
-void orc_collide_g(const double *g, const double *Q, const double *u, double *gout) {
-    double Nm[Q7 * Q7], Ninv[Q7 * Q7];
+void orc_collide_g(const real *g, const real *Q, const real *u, real *gout) {
+    real Nm[Q7 * Q7], Ninv[Q7 * Q7];
     build_N(Nm);
     invert(Q7, Nm, Ninv);
     collide_g(Nm, Ninv, Q, g, u, gout);
 }
+
+/* Liquid-side front gradient and ghost temperature of one column (the
+   Eq. 6 stencil and the interface ghost rule), for unit tests. */
+double orc_front_gradient(const double *Tcol, int n, double s, double Tw, double Tm) {
+    return front_gradient(Tcol, n, s, Tw, Tm);
+}
+
+double orc_ghost_T(const double *Tcol, int n, double s, double Tw, double Tm) {
+    return ghost_T(Tcol, n, s, Tw, Tm);
+}
+#else
+/* --------------------------------------------- complex-step (tangent) API */
+
+/* Perturb Ra by i*h*dRa and the heated-wall field by i*h*dTw (h folded into
+   the caller's direction), re-deriving the lattice parameters; the state
+   keeps its real part.  Call right after orc_create. */
+int orc_cs_perturb(orc_sim *S, double Ra_im, const double *Thw_im) {
+    S->Ra_im = Ra_im;
+    if (derive(S) != ORC_OK) return ORC_EINVAL;
+    if (Thw_im)
+        for (long col = 0; col < S->ncols; ++col) S->Thw[col] = RE(S->Thw[col]) + I * Thw_im[col];
+    refresh_ghosts(S);
+    return ORC_OK;
+}
+
+/* Real and imaginary parts of the front heights and of the liquid fraction. */
+void orc_cs_get_s(const orc_sim *S, double *re, double *im, double *lf_re, double *lf_im) {
+    real acc = 0.0;
+    for (long col = 0; col < S->ncols; ++col) {
+        if (re) re[col] = creal(S->s[col]);
+        if (im) im[col] = cimag(S->s[col]);
+        acc += S->s[col];
+    }
+    acc /= ((double)S->H * (double)S->ncols);
+    if (lf_re) *lf_re = creal(acc);
+    if (lf_im) *lf_im = cimag(acc);
+}
+#endif
