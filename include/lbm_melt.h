@@ -203,6 +203,29 @@ lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, in
 const char *lbm_melt_last_error(const lbm_melt *h);
 void lbm_melt_destroy(lbm_melt *h);
 
+/* ----------------------------------------------------------------- adjoint
+   Gradients of a function of the final front S with respect to the
+   heated-wall temperature field and Ra, by a hand-written adjoint of the
+   step (Eqs. 1-6) with the phase flags held at their recorded values.
+
+   lbm_melt_tape_forward advances the handle by `steps` steps (as
+   lbm_melt_step) and keeps a checkpoint of the state every ckpt_every steps
+   (<= 0: ceil(sqrt(steps))).  The heated-wall field must be set before (no
+   change pending) and stays fixed during the recorded run.
+
+   lbm_melt_tape_backward takes seed_dL_dS = dL/dS of the final front (one
+   value per column) and returns dL_dTh = dL/d(heated-wall temperature) per
+   column and dL_dparams[5] = {dL/dRa, dL/ds_nu, dL/ds_alpha, dL/dcoef,
+   dL/d(g beta)} (coef = alpha Ste / (Th - Tm), the Eq. 6 factor; dL/dRa
+   chains these through the parameter map of lbm_melt_derive).  Segments are
+   recomputed from their checkpoints with one snapshot per step, then
+   reversed; the handle is back in its final state afterwards.  Synchronises. */
+lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every);
+lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed_dL_dS, double *dL_dTh, double *dL_dparams,
+                                  int ptr_kind);
+/* Release the recorded run. */
+lbm_status lbm_melt_tape_clear(lbm_melt *h);
+
 /* ------------------------------------------------------------------ ensemble
    A batch of independent cavities of uneven sizes and parameters advanced in
    lockstep by one persistent kernel launch per run of steps: each step covers

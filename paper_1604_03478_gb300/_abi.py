@@ -80,6 +80,9 @@ def load() -> C.CDLL:
         "lbm_melt_set_launch": (C.c_int, [vp, C.c_int, C.c_int]),
         "lbm_melt_kernel_time": (C.c_int, [vp, dp, C.POINTER(C.c_longlong), C.c_int]),
         "lbm_melt_last_error": (C.c_char_p, [vp]),
+        "lbm_melt_tape_forward": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
+        "lbm_melt_tape_backward": (C.c_int, [vp, vp, vp, vp, C.c_int]),
+        "lbm_melt_tape_clear": (C.c_int, [vp]),
         "lbm_ensemble_create": (C.c_int, [C.c_int, C.POINTER(lbm_melt_case), vp, C.POINTER(vp)]),
         "lbm_ensemble_step": (C.c_int, [vp, C.c_longlong]),
         "lbm_ensemble_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),

@@ -170,6 +170,24 @@ class Cavity:
         self._check(_abi.load().lbm_melt_get_info(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in i._fields_}
 
+    PARAM_KEYS = ("Ra", "s_nu", "s_alpha", "coef", "gbeta")
+
+    def tape_forward(self, steps, ckpt_every=0):
+        """Advance `steps` steps recording checkpoints for tape_backward."""
+        self._check(_abi.load().lbm_melt_tape_forward(self._h, int(steps), int(ckpt_every)))
+
+    def tape_backward(self, seed):
+        """dL/d(heated-wall field) per column and the parameter sensitivities
+        for dL/dS = seed of the final front."""
+        seed = np.ascontiguousarray(seed, np.float64).reshape(self.ncols)
+        dth = np.zeros(self.ncols, np.float64)
+        dpar = np.zeros(5, np.float64)
+        self._check(_abi.load().lbm_melt_tape_backward(self._h, _ptr(seed), _ptr(dth), _ptr(dpar), 0))
+        return dth.reshape(self.cols_shape), dict(zip(self.PARAM_KEYS, dpar.tolist()))
+
+    def tape_clear(self):
+        self._check(_abi.load().lbm_melt_tape_clear(self._h))
+
     def set_launch(self, bx=0, by=0):
         self._check(_abi.load().lbm_melt_set_launch(self._h, int(bx), int(by)))
 

@@ -1,0 +1,703 @@
+// adjoint.cu -- hand-written adjoint of the melting step (Li, Yang & Zhang,
+// arXiv:1604.03478, Eqs. 1-6) for gradients of a function of the final
+// front S with respect to the heated-wall temperature field and Ra.
+//
+// The step is differentiated with the phase flags held at their forward
+// values (the map is smooth between flips).  Forward: one step maps the
+// natural state (f, g, s) at t to t+1 by collision (Eqs. 1-5; the first
+// solid node of each column takes the ghost populations prepared from the
+// state at t), pull streaming with the wall rules, the front update (Eq. 6)
+// and the flip (a newly liquid node's f is reset to a constant).  Reverse
+// step t, from the adjoint at t+1 to the adjoint at t:
+//   k_adj_front  Eq. 6 backwards: lambda_s(t+1) -> lambda_s(t), the T of
+//                the two stencil nodes at t+1, the wall field, d/d coef;
+//   k_adj_slopes the in-plane slope terms of Eq. 6 into the neighbours;
+//   k_adj_node   streaming transposed (a push becomes a gather under the
+//                flags of t) and the collision Jacobian transposed, FP32,
+//                with d/d s_nu, s_alpha, g*beta in FP64 block partials;
+//   k_adj_ghost  the ghost populations of the state at t backwards.
+// The forward is recorded with sqrt(N)-style checkpoints; each segment is
+// recomputed forward with a natural-layout snapshot per step, then reversed.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_melt.h"
+#include "handle.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+#define LBM_API extern "C" __attribute__((visibility("default")))
+
+namespace lbm {
+
+// -------------------------------------------------------------- snapshot
+// Natural shifted state of one time level: fh (19 x N, zero at solid nodes)
+// then gh (7 x N), FP32.
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_snapshot(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+                                                  const int *__restrict__ js, const float *__restrict__ thw,
+                                                  int inflight, float *__restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long c = node_index(p, x, y, z);
+    const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
+    float g[7], f[19];
+    gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
+    const bool liq = a < js[col];
+    if (liq) gather_f<ST, FACE>(p, F, js, x, y, z, inflight != 0, f);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) out[i * p.N + c] = liq ? f[i] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) out[(19 + i) * p.N + c] = g[i];
+}
+
+// ------------------------------------------------- collision, transposed
+// Given the state (fh, gh) of a liquid node and the adjoint of its
+// post-collision populations (lf, lg), return the adjoint of the
+// pre-collision populations (of, og) and add d/d s_nu, s_alpha, g*beta.
+__device__ __forceinline__ void collide_adjoint(const KP &p, const float (&f)[19], const float (&g)[7],
+                                                const float (&lf)[19], const float (&lg)[7], float (&of)[19],
+                                                float (&og)[7], float &dsnu, float &dsal, float &dgb) {
+    // forward quantities
+    const float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    const float T = Th + p.Tm;
+    const float Fz = p.gbeta * Th;
+    float S[9], D[9], m[19];
+#pragma unroll
+    for (int P = 0; P < 9; ++P) {
+        S[P] = f[pf(P)] + f[opp(pf(P))];
+        D[P] = f[pf(P)] - f[opp(pf(P))];
+    }
+    moments_pairs<0>(f[0], S, D, m);
+    const float ux = m[3], uy = m[5], uz = m[7] + 0.5f * Fz;
+    const float uzF = uz * Fz;
+    const float pxx = 2.0f * ux * ux - uy * uy - uz * uz;
+    const float pww = uy * uy - uz * uz;
+    // adjoint of the moment deltas: A_k = (M lf)_k / |row k|^2
+    float Sl[9], Dl[9], Ml[19], A[19];
+#pragma unroll
+    for (int P = 0; P < 9; ++P) {
+        Sl[P] = lf[pf(P)] + lf[opp(pf(P))];
+        Dl[P] = lf[pf(P)] - lf[opp(pf(P))];
+    }
+    moments_pairs<0>(lf[0], Sl, Dl, Ml);
+    scale_by_inverse_norms<0>(Ml, A);
+    const float se = p.s_e, seps = p.s_eps, sq = p.s_q, snu = p.s_nu, spi = p.s_pi, sm = p.s_m;
+    float lm[19];
+    lm[1] = -se * A[1];
+    lm[2] = -seps * A[2];
+    lm[4] = -sq * A[4];
+    lm[6] = -sq * A[6];
+    lm[8] = -sq * A[8];
+    lm[9] = -snu * A[9];
+    lm[10] = -spi * A[10];
+    lm[11] = -snu * A[11];
+    lm[12] = -spi * A[12];
+    lm[13] = -snu * A[13];
+    lm[14] = -snu * A[14];
+    lm[15] = -snu * A[15];
+    lm[16] = -sm * A[16];
+    lm[17] = -sm * A[17];
+    lm[18] = -sm * A[18];
+    const float lrho = -11.0f * se * A[1] + 3.0f * seps * A[2];
+    const float luu = 19.0f * se * A[1] - 5.5f * seps * A[2];
+    const float luzF = 38.0f * (1.0f - 0.5f * se) * A[1] - 11.0f * (1.0f - 0.5f * seps) * A[2] -
+                       2.0f * (1.0f - 0.5f * snu) * (A[9] + A[11]) + (1.0f - 0.5f * spi) * (A[10] + A[12]);
+    const float lpxx = snu * A[9] - 0.5f * spi * A[10];
+    const float lpww = snu * A[11] - 0.5f * spi * A[12];
+    const float lxy = snu * A[13], lyz = snu * A[14], lxz = snu * A[15];
+    const float lyF = (1.0f - 0.5f * snu) * A[14], lxF = (1.0f - 0.5f * snu) * A[15];
+    float lux = -(2.0f / 3.0f) * sq * A[4] + 2.0f * ux * luu + 4.0f * ux * lpxx + uy * lxy + uz * lxz + Fz * lxF;
+    float luy = -(2.0f / 3.0f) * sq * A[6] + 2.0f * uy * luu - 2.0f * uy * lpxx + 2.0f * uy * lpww + ux * lxy +
+                uz * lyz + Fz * lyF;
+    float luz = -(2.0f / 3.0f) * sq * A[8] + 2.0f * uz * luu - 2.0f * uz * lpxx - 2.0f * uz * lpww + uy * lyz +
+                ux * lxz + Fz * luzF;
+    float lFz = A[7] - (2.0f / 3.0f) * (1.0f - 0.5f * sq) * A[8] + uz * luzF + uy * lyF + ux * lxF;
+    dsnu += A[9] * (-(m[9] - pxx) + uzF) + A[11] * (-(m[11] - pww) + uzF) - A[13] * (m[13] - ux * uy) +
+            A[14] * (-(m[14] - uy * uz) - 0.5f * uy * Fz) + A[15] * (-(m[15] - ux * uz) - 0.5f * ux * Fz);
+    // D3Q7: B_k = (N lg)_k / |row k|^2
+    const float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
+    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+    const float B1 = (lg[1] - lg[2]) * i1, B2 = (lg[3] - lg[4]) * i1, B3 = (lg[5] - lg[6]) * i1;
+    const float B4 = (6.0f * lg[0] - (lg[1] + lg[2] + lg[3] + lg[4] + lg[5] + lg[6])) * i4;
+    const float B5 = (2.0f * (lg[1] + lg[2]) - (lg[3] + lg[4] + lg[5] + lg[6])) * i5;
+    const float B6 = ((lg[3] + lg[4]) - (lg[5] + lg[6])) * i6;
+    const float sa = p.s_alpha;
+    float ln[7];
+    ln[1] = -sa * B1;
+    ln[2] = -sa * B2;
+    ln[3] = -sa * B3;
+    ln[4] = -p.s_g4 * B4;
+    ln[5] = -p.s_g5 * B5;
+    ln[6] = -p.s_g5 * B6;
+    lux += sa * T * B1;
+    luy += sa * T * B2;
+    luz += sa * T * B3;
+    float lTh = sa * (ux * B1 + uy * B2 + uz * B3) + 0.75f * p.s_g4 * B4;
+    dsal += -((n1 - ux * T) * B1 + (n2 - uy * T) * B2 + (n3 - uz * T) * B3);
+    // through u_z = j_z + F/2 and F = g beta (T - Tm)
+    lFz += 0.5f * luz;
+    lTh += p.gbeta * lFz;
+    dgb += Th * lFz;
+    lm[0] = lrho;
+    lm[3] = lux;
+    lm[5] = luy;
+    lm[7] = luz;
+    ln[0] = lTh;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) of[i] = lf[i];
+    of[0] = pcol_all<0, 0, false>(lm, of[0]);
+    add_back_pairs_all<0>(of, lm);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) og[i] = lg[i];
+    add_back7_all<0>(og, ln);
+}
+
+// Temperature of node j of column col in a snapshot; cn receives its index.
+template <int FACE>
+__device__ __forceinline__ double snap_T(const KP &p, const float *snap, int col, int j, long long &cn) {
+    int x, y, z;
+    column_node<FACE>(p, col, j, x, y, z);
+    cn = node_index(p, x, y, z);
+    double t = 0.0;
+    for (int i = 0; i < 7; ++i) t += (double)snap[(19 + i) * p.N + cn];
+    return p.Tm_d + t;
+}
+
+// ------------------------------------------------- reverse of Eq. 6
+// Per column: lambda_s(t) own part, slope partials wp/wq, the stencil
+// nodes' temperature adjoint added to lam1 (adjoint of the state at t+1),
+// the wall field, and d/d coef.
+template <int FACE>
+__global__ void __launch_bounds__(128) k_adj_front(KP p, const float *__restrict__ snap1, const double *__restrict__ s,
+                                                   const float *__restrict__ thw, const double *__restrict__ lams1,
+                                                   double *__restrict__ lams0, double *__restrict__ wp,
+                                                   double *__restrict__ wq, float *__restrict__ lam1,
+                                                   double *__restrict__ lthw, double *__restrict__ lcoef) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    const int P1 = p.P1, P2 = p.P2, H = p.H;
+    const int pp = col % P1, q = col / P1;
+    const double sc = s[col], Tm = p.Tm_d, Tw = (double)thw[col];
+    const double sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
+    const double sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
+    const int k = guarded_node(sc, H);
+    double G, dGds, dGdy0 = 0.0, dGdy1 = 0.0, dGdTw = 0.0;
+    long long c1 = 0, c0 = 0;
+    if (k < 0) {
+        G = (Tm - Tw) / sc;
+        dGds = -(Tm - Tw) / (sc * sc);
+        dGdTw = -1.0 / sc;
+    } else {
+        const double y1 = snap_T<FACE>(p, snap1, col, k, c1), x1 = k + 0.5;
+        const double x0 = k >= 1 ? k - 0.5 : 0.0;
+        const double y0 = k >= 1 ? snap_T<FACE>(p, snap1, col, k - 1, c0) : Tw;
+        const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
+        G = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
+        dGdy0 = d1 / (h * d0);
+        dGdy1 = -d0 / (h * d1);
+        dGds = (y0 - Tm) / (d0 * d0) + (y1 - Tm) / (d1 * d1);
+    }
+    const double fac = 1.0 + sp * sp + sq * sq;
+    const double v = p.coef * fac * (-G);
+    const double sn = sc + v;
+    const double L = lams1[col];
+    if (!(sn >= 0.5) || sn > (double)H) {  // clamped: s(t+1) does not depend on anything
+        lams0[col] = 0.0;
+        wp[col] = 0.0;
+        wq[col] = 0.0;
+        return;
+    }
+    const double a = L * p.coef * fac;  // lambda times d v / d(-G)
+    lams0[col] = L - a * dGds;
+    wp[col] = L * p.coef * (-G) * 2.0 * sp;
+    wq[col] = L * p.coef * (-G) * 2.0 * sq;
+    lcoef[col] += L * fac * (-G);
+    if (k >= 0) {
+        const float lT1 = (float)(-a * dGdy1);
+        for (int i = 0; i < 7; ++i) lam1[(19 + i) * p.N + c1] += lT1;
+        if (k >= 1) {
+            const float lT0 = (float)(-a * dGdy0);
+            for (int i = 0; i < 7; ++i) lam1[(19 + i) * p.N + c0] += lT0;
+        } else {
+            lthw[col] += -a * dGdy0;
+        }
+    } else {
+        lthw[col] += -a * dGdTw;
+    }
+}
+
+// The slopes s_p, s_q of column c' read the fronts of its neighbours (with a
+// mirror at the side walls); gather their d/d s back to each column.
+__global__ void __launch_bounds__(128) k_adj_slopes(KP p, const double *__restrict__ wp,
+                                                    const double *__restrict__ wq, double *__restrict__ lams0) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    const int P1 = p.P1, P2 = p.P2;
+    const int pp = col % P1, q = col / P1;
+    double acc = 0.0;
+    if (P1 > 1) {
+        if (pp >= 1) acc += 0.5 * wp[col - 1];       // column pp-1 reads s[pp] as its upper neighbour
+        if (pp <= P1 - 2) acc -= 0.5 * wp[col + 1];  // column pp+1 reads s[pp] as its lower neighbour
+        if (pp == 0) acc -= 0.5 * wp[col];           // mirror: s[-1] = s[0]
+        if (pp == P1 - 1) acc += 0.5 * wp[col];      // mirror: s[P1] = s[P1-1]
+    }
+    if (P2 > 1) {
+        if (q >= 1) acc += 0.5 * wq[col - P1];
+        if (q <= P2 - 2) acc -= 0.5 * wq[col + P1];
+        if (q == 0) acc -= 0.5 * wq[col];
+        if (q == P2 - 1) acc += 0.5 * wq[col];
+    }
+    lams0[col] += acc;
+}
+
+// ----------------------------------------- streaming and collision, reversed
+template <int FACE>
+__global__ void __launch_bounds__(128) k_adj_node(KP p, const float *__restrict__ snap, const int *__restrict__ js,
+                                                  const float *__restrict__ lam1, float *__restrict__ lam0,
+                                                  float *__restrict__ lgpost, double *__restrict__ lthw,
+                                                  double *__restrict__ part) {
+    __shared__ double sh[3][128];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    float dsnu = 0.0f, dsal = 0.0f, dgb = 0.0f;
+    if (x < p.nx && y < p.ny) {
+        const long long c = node_index(p, x, y, z);
+        const long long N = p.N;
+        const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
+        const int jsc = js[col];
+        // heated-wall link: the node next to the wall receives
+        // -g*_opp + 2 w (Tw - Tm) along the heating axis
+        if (a == 0) {
+            const int iin = FACE == 0 ? 3 : 5;
+            lthw[col] += 2.0 * (double)w7(iin) * (double)lam1[(19 + iin) * N + c];
+        }
+        if (a > jsc) {
+#pragma unroll
+            for (int i = 0; i < 26; ++i) lam0[i * N + c] = 0.0f;
+        } else {
+            // g*: every node streams g; the transpose of the pull is a gather
+            float lg[7];
+            lg[0] = lam1[19 * N + c];
+#pragma unroll
+            for (int i = 1; i < 7; ++i) {
+                if (inside(p, x + tx(i), y + ty(i), z + tz(i))) {
+                    lg[i] = lam1[(19 + i) * N + c + off7<FACE>(p, i)];
+                } else {
+                    const int w = wall_of_link<FACE>(i);
+                    const float v = lam1[(19 + opp7(i)) * N + c];
+                    lg[i] = w == 3 ? v : -v;
+                }
+            }
+            if (a == jsc) {  // ghost node: its post-collision g came from the ghost rule
+#pragma unroll
+                for (int i = 0; i < 7; ++i) lgpost[(long long)i * p.ncols + col] = lg[i];
+#pragma unroll
+                for (int i = 0; i < 26; ++i) lam0[i * N + c] = 0.0f;
+            } else {
+                float lf[19], f[19], g[7], of[19], og[7];
+                lf[0] = lam1[c];
+#pragma unroll
+                for (int i = 1; i < 19; ++i) {
+                    if (liquid_at<FACE>(p, js, x + ex(i), y + ey(i), z + ez(i)))
+                        lf[i] = lam1[i * N + c + off19<FACE>(p, i)];
+                    else
+                        lf[i] = lam1[opp(i) * N + c];
+                }
+#pragma unroll
+                for (int i = 0; i < 19; ++i) f[i] = snap[i * N + c];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) g[i] = snap[(19 + i) * N + c];
+                collide_adjoint(p, f, g, lf, lg, of, og, dsnu, dsal, dgb);
+#pragma unroll
+                for (int i = 0; i < 19; ++i) lam0[i * N + c] = of[i];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) lam0[(19 + i) * N + c] = og[i];
+            }
+        }
+    }
+    sh[0][tid] = dsnu;
+    sh[1][tid] = dsal;
+    sh[2][tid] = dgb;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (tid < w) {
+            sh[0][tid] += sh[0][tid + w];
+            sh[1][tid] += sh[1][tid + w];
+            sh[2][tid] += sh[2][tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid < 3) {
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        part[b * 3 + tid] += sh[tid][0];
+    }
+}
+
+// ---------------------------------------------- ghost populations, reversed
+// g*_ghost = w (T_ghost - Tm) + N^T D^-1 (I - Q)(n_L - n^eq_L), with T_ghost
+// on the line through (s, Tm) and the guarded node (or the wall).
+template <int FACE>
+__global__ void __launch_bounds__(128) k_adj_ghost(KP p, const float *__restrict__ snap, const int *__restrict__ js,
+                                                   const double *__restrict__ s, const float *__restrict__ thw,
+                                                   const float *__restrict__ lgpost, float *__restrict__ lam0,
+                                                   double *__restrict__ lams0, double *__restrict__ lthw,
+                                                   double *__restrict__ lsal, double *__restrict__ lgb) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    const int H = p.H, jn = js[col];
+    if (jn >= H) return;
+    const long long N = p.N;
+    const double sn = s[col], Tm = p.Tm_d, Tw = (double)thw[col];
+    const double yg = jn + 0.5;
+    float lgp[7];
+    double lTG = 0.0;
+    for (int i = 0; i < 7; ++i) {
+        lgp[i] = lgpost[(long long)i * p.ncols + col];
+        lTG += (double)w7(i) * lgp[i];
+    }
+    const int kg = guarded_node(sn, H);
+    if (kg < 0) {
+        lthw[col] += -(yg - sn) / sn * lTG;
+        lams0[col] += (Tm - Tw) * (-yg / (sn * sn)) * lTG;
+    } else {
+        int x, y, z;
+        column_node<FACE>(p, col, kg, x, y, z);
+        const long long ck = node_index(p, x, y, z);
+        double Tk = Tm;
+        for (int i = 0; i < 7; ++i) Tk += (double)snap[(19 + i) * N + ck];
+        const double yk = kg + 0.5, r = (yg - sn) / (sn - yk);
+        const float lTk = (float)(-r * lTG);
+        for (int i = 0; i < 7; ++i) lam0[(19 + i) * N + ck] += lTk;
+        lams0[col] += (Tm - Tk) * (-(yg - yk) / ((sn - yk) * (sn - yk))) * lTG;
+    }
+    if (jn < 1) return;
+    int x, y, z;
+    column_node<FACE>(p, col, jn - 1, x, y, z);
+    const long long cL = node_index(p, x, y, z);
+    float gL[7], fL[19];
+    for (int i = 0; i < 7; ++i) gL[i] = snap[(19 + i) * N + cL];
+    for (int i = 0; i < 19; ++i) fL[i] = snap[i * N + cL];
+    float Th = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    for (int i = 0; i < 7; ++i) Th += gL[i];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) { jx += ex(i) * fL[i]; jy += ey(i) * fL[i]; jz += ez(i) * fL[i]; }
+    const float TL = Th + p.Tm;
+    const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
+    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+    const float Nl1 = lgp[1] - lgp[2], Nl2 = lgp[3] - lgp[4], Nl3 = lgp[5] - lgp[6];
+    const float Nl4 = 6.0f * lgp[0] - (lgp[1] + lgp[2] + lgp[3] + lgp[4] + lgp[5] + lgp[6]);
+    const float Nl5 = 2.0f * (lgp[1] + lgp[2]) - (lgp[3] + lgp[4] + lgp[5] + lgp[6]);
+    const float Nl6 = (lgp[3] + lgp[4]) - (lgp[5] + lgp[6]);
+    const float d1 = (gL[1] - gL[2]) - ux * TL, d2 = (gL[3] - gL[4]) - uy * TL, d3 = (gL[5] - gL[6]) - uz * TL;
+    lsal[col] += -(double)(i1 * (Nl1 * d1 + Nl2 * d2 + Nl3 * d3));
+    const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
+    float mu[7];
+    mu[0] = 0.0f;
+    mu[1] = ra * i1 * Nl1;
+    mu[2] = ra * i1 * Nl2;
+    mu[3] = ra * i1 * Nl3;
+    mu[4] = r4 * i4 * Nl4;
+    mu[5] = r5 * i5 * Nl5;
+    mu[6] = r5 * i6 * Nl6;
+    const float lux = -mu[1] * TL, luy = -mu[2] * TL, luz = -mu[3] * TL;
+    const float lTh = -(mu[1] * ux + mu[2] * uy + mu[3] * uz) - 0.75f * mu[4] + 0.5f * p.gbeta * luz;
+    lgb[col] += 0.5 * (double)Th * (double)luz;
+    float og[7];
+    for (int i = 0; i < 7; ++i) og[i] = lTh;
+    add_back7_all<0>(og, mu);
+    for (int i = 0; i < 7; ++i) lam0[(19 + i) * N + cL] += og[i];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) lam0[i * N + cL] += ex(i) * lux + ey(i) * luy + ez(i) * luz;
+}
+
+// Deterministic FP64 sum of n values (one block), times scale, added to *out.
+__global__ void __launch_bounds__(256) k_sum_into(const double *__restrict__ v, long long n, long long stride,
+                                                  double *__restrict__ out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += v[i * stride];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += sh[0];
+}
+
+}  // namespace lbm
+
+// ------------------------------------------------------------------ tape
+
+struct lbm_tape {
+    long long T, C, nseg;
+    size_t ck_bytes;
+    std::vector<void *> ck;          // device checkpoints, one per segment
+    std::vector<int> ck_cur, ck_inflight;
+    std::vector<long long> ck_steps;
+};
+
+namespace {
+
+lbm_status tape_err(lbm_melt *h, lbm_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof h->err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define TCK(call, where)                                                                                   \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return tape_err(h, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", where,  \
+                            cudaGetErrorString(e_));                                                       \
+    } while (0)
+
+// Layout of a checkpoint: the nine state arrays of a handle, each starting
+// on a 256-byte boundary.  Returns the total size; dev/sz/off describe them.
+size_t state_layout(const lbm_melt *h, void *dev[9], size_t sz[9], size_t off[9]) {
+    const size_t es = h->precision == 1 ? 2 : 4, nc = (size_t)h->kp.ncols;
+    void *d[9] = {h->F, h->G, h->js[0], h->js[1], h->nb[0], h->nb[1], h->s[0], h->s[1], h->gpost};
+    const size_t b[9] = {19 * (size_t)h->kp.ld * es, 7 * (size_t)h->kp.ld * es, nc * 4, nc * 4, nc * 4, nc * 4,
+                         nc * 8, nc * 8, 7 * nc * 4};
+    size_t o = 0;
+    for (int k = 0; k < 9; ++k) {
+        if (dev) dev[k] = d[k];
+        if (sz) sz[k] = b[k];
+        if (off) off[k] = o;
+        o += (b[k] + 255) / 256 * 256;
+    }
+    return o;
+}
+
+// copy the handle's state to (dir = 0) or from (dir = 1) a checkpoint buffer
+lbm_status move_state(lbm_melt *h, unsigned char *buf, int dir) {
+    void *dev[9];
+    size_t sz[9], off[9];
+    state_layout(h, dev, sz, off);
+    for (int k = 0; k < 9; ++k) {
+        void *a = dev[k], *b = buf + off[k];
+        TCK(cudaMemcpyAsync(dir ? a : b, dir ? b : a, sz[k], cudaMemcpyDeviceToDevice, h->stream), "state copy");
+    }
+    return LBM_OK;
+}
+
+void free_tape(lbm_melt *h) {
+    lbm_tape *t = (lbm_tape *)h->tape;
+    if (!t) return;
+    cudaStreamSynchronize(h->stream);
+    for (void *p : t->ck) cudaFree(p);
+    delete t;
+    h->tape = nullptr;
+}
+
+}  // namespace
+
+void lbm_tape_free(lbm_melt *h) { free_tape(h); }
+
+LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every) {
+    if (!h) return LBM_EINVAL;
+    if (steps < 1) return tape_err(h, LBM_EINVAL, "steps must be >= 1");
+    if (h->thw_pending)
+        return tape_err(h, LBM_EINVAL, "set the heated-wall field before recording (no change may be pending)");
+    if (ckpt_every <= 0) ckpt_every = (long long)std::ceil(std::sqrt((double)steps));
+    free_tape(h);
+    lbm_tape *t = new (std::nothrow) lbm_tape();
+    if (!t) return LBM_ENOMEM;
+    h->tape = t;
+    t->T = steps;
+    t->C = ckpt_every;
+    t->nseg = (steps + ckpt_every - 1) / ckpt_every;
+    t->ck_bytes = state_layout(h, nullptr, nullptr, nullptr);
+    for (long long sgm = 0; sgm < t->nseg; ++sgm) {
+        void *buf = nullptr;
+        cudaError_t e = cudaMalloc(&buf, t->ck_bytes);
+        if (e != cudaSuccess) {
+            free_tape(h);
+            return tape_err(h, LBM_ENOMEM, "checkpoint %lld of %lld: %s", sgm, t->nseg, cudaGetErrorString(e));
+        }
+        t->ck.push_back(buf);
+        t->ck_cur.push_back(h->cur);
+        t->ck_inflight.push_back(h->inflight);
+        t->ck_steps.push_back(h->steps);
+        lbm_status st = move_state(h, (unsigned char *)buf, 0);
+        if (st != LBM_OK) return st;
+        const long long n = std::min(ckpt_every, steps - sgm * ckpt_every);
+        st = lbm_melt_step(h, n);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_tape_clear(lbm_melt *h) {
+    if (!h) return LBM_EINVAL;
+    free_tape(h);
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, double *dL_dTh, double *dL_dparams,
+                                          int ptr_kind) {
+    if (!h || !seed) return LBM_EINVAL;
+    lbm_tape *t = (lbm_tape *)h->tape;
+    if (!t) return tape_err(h, LBM_EINVAL, "no recorded run (call lbm_melt_tape_forward first)");
+    const lbm::KP &p = h->kp;
+    const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
+    const long long C = t->C;
+    const dim3 blk = lbm::node_block(p), grd = lbm::node_grid(p, blk);
+    const size_t nblk = (size_t)grd.x * grd.y * grd.z;
+    const int cgrid = (int)((nc + 127) / 128);
+    // buffers
+    unsigned char *fin = nullptr;
+    float *snap = nullptr, *lam[2] = {nullptr, nullptr}, *lgpost = nullptr;
+    double *snap_s = nullptr, *lams[2] = {nullptr, nullptr}, *wp = nullptr, *wq = nullptr, *lthw = nullptr;
+    double *part = nullptr, *lsal = nullptr, *lgb = nullptr, *lcoef = nullptr, *acc = nullptr;
+    int *snap_js = nullptr;
+    struct Alloc { void **p; size_t b; } al[] = {
+        {(void **)&fin, t->ck_bytes}, {(void **)&snap, (size_t)(C + 1) * 26 * N * 4},
+        {(void **)&snap_s, (size_t)(C + 1) * nc * 8}, {(void **)&snap_js, (size_t)(C + 1) * nc * 4},
+        {(void **)&lam[0], 26 * N * 4}, {(void **)&lam[1], 26 * N * 4}, {(void **)&lgpost, 7 * nc * 4},
+        {(void **)&lams[0], nc * 8}, {(void **)&lams[1], nc * 8}, {(void **)&wp, nc * 8}, {(void **)&wq, nc * 8},
+        {(void **)&lthw, nc * 8}, {(void **)&part, nblk * 3 * 8}, {(void **)&lsal, nc * 8},
+        {(void **)&lgb, nc * 8}, {(void **)&lcoef, nc * 8}, {(void **)&acc, 4 * 8}};
+    lbm_status st = LBM_OK;
+    auto cleanup = [&]() {
+        for (auto &a : al) cudaFree(*a.p);
+    };
+    for (auto &a : al) {
+        cudaError_t e = cudaMalloc(a.p, a.b);
+        if (e != cudaSuccess) {
+            cleanup();
+            return tape_err(h, LBM_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+        }
+    }
+#define BCK(call, where)                                                             \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            cleanup();                                                               \
+            return tape_err(h, LBM_ECUDA, "%s: %s", where, cudaGetErrorString(e_));  \
+        }                                                                            \
+    } while (0)
+    // the final state is restored at the end
+    const int fin_cur = h->cur, fin_inflight = h->inflight;
+    const long long fin_steps = h->steps;
+    if ((st = move_state(h, fin, 0)) != LBM_OK) { cleanup(); return st; }
+    for (auto &a : al)
+        if (a.p != (void **)&fin && a.p != (void **)&snap) BCK(cudaMemsetAsync(*a.p, 0, a.b, h->stream), "zero");
+    BCK(cudaMemcpyAsync(lams[1], seed, nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream), "seed");
+    auto snapshot = [&](long long j) -> lbm_status {
+        lbm::Bufs b;
+        std::memset(&b, 0, sizeof b);
+        b.F = h->F; b.G = h->G; b.js = h->js[h->cur];
+        const float *thw = h->thw_cur;
+        float *out = snap + (size_t)j * 26 * N;
+        if (h->precision == 1) {
+            if (h->face == 0) lbm::k_snapshot<__half, 0><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, thw, h->inflight, out);
+            else lbm::k_snapshot<__half, 1><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, thw, h->inflight, out);
+        } else {
+            if (h->face == 0) lbm::k_snapshot<float, 0><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, thw, h->inflight, out);
+            else lbm::k_snapshot<float, 1><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, thw, h->inflight, out);
+        }
+        TCK(cudaGetLastError(), "snapshot");
+        TCK(cudaMemcpyAsync(snap_s + (size_t)j * nc, h->s[h->cur], nc * 8, cudaMemcpyDeviceToDevice, h->stream), "snap s");
+        TCK(cudaMemcpyAsync(snap_js + (size_t)j * nc, h->js[h->cur], nc * 4, cudaMemcpyDeviceToDevice, h->stream), "snap js");
+        return LBM_OK;
+    };
+    const float *thw = h->thw_cur;
+    for (long long sgm = t->nseg - 1; sgm >= 0 && st == LBM_OK; --sgm) {
+        const long long len = std::min(C, t->T - sgm * C);
+        if ((st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
+        h->cur = t->ck_cur[sgm];
+        h->inflight = t->ck_inflight[sgm];
+        h->steps = t->ck_steps[sgm];
+        if ((st = snapshot(0)) != LBM_OK) break;
+        for (long long j = 1; j <= len && st == LBM_OK; ++j) {
+            if ((st = lbm_melt_step(h, 1)) != LBM_OK) break;
+            st = snapshot(j);
+        }
+        if (st != LBM_OK) break;
+        for (long long j = len - 1; j >= 0; --j) {
+            const float *s1 = snap + (size_t)(j + 1) * 26 * N, *s0 = snap + (size_t)j * 26 * N;
+            const double *st_s = snap_s + (size_t)j * nc;
+            const int *st_js = snap_js + (size_t)j * nc;
+            if (h->face == 0) {
+                lbm::k_adj_front<0><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
+                lbm::k_adj_slopes<<<cgrid, 128, 0, h->stream>>>(p, wp, wq, lams[0]);
+                lbm::k_adj_node<0><<<grd, blk, 0, h->stream>>>(p, s0, st_js, lam[1], lam[0], lgpost, lthw, part);
+                lbm::k_adj_ghost<0><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb);
+            } else {
+                lbm::k_adj_front<1><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
+                lbm::k_adj_slopes<<<cgrid, 128, 0, h->stream>>>(p, wp, wq, lams[0]);
+                lbm::k_adj_node<1><<<grd, blk, 0, h->stream>>>(p, s0, st_js, lam[1], lam[0], lgpost, lthw, part);
+                lbm::k_adj_ghost<1><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb);
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { st = tape_err(h, LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e)); break; }
+            std::swap(lam[0], lam[1]);
+            std::swap(lams[0], lams[1]);
+        }
+    }
+    if (st == LBM_OK) {
+        // parameter sensitivities: acc = {d/ds_nu, d/ds_alpha, d/dcoef, d/dgbeta}
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(part, (long long)nblk, 3, acc);
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(part + 1, (long long)nblk, 3, acc + 1);
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(lsal, (long long)nc, 1, acc + 1);
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(lcoef, (long long)nc, 1, acc + 2);
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(part + 2, (long long)nblk, 3, acc + 3);
+        lbm::k_sum_into<<<1, 256, 0, h->stream>>>(lgb, (long long)nc, 1, acc + 3);
+        double a[4] = {0, 0, 0, 0};
+        cudaError_t e = cudaMemcpyAsync(a, acc, sizeof a, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && dL_dTh)
+            e = cudaMemcpyAsync(dL_dTh, lthw, nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = tape_err(h, LBM_ECUDA, "adjoint outputs: %s", cudaGetErrorString(e));
+        if (st == LBM_OK && dL_dparams) {
+            // chain to Ra: with derive_from_Ra, nu = U0 H sqrt(Pr/Ra), alpha = nu/Pr,
+            // s_nu = 1/(3 nu + 1/2), s_alpha = 1/(4 alpha + 1/2), coef = alpha Ste/(Th - Tm)
+            // and g beta = U0^2 / (H (Th - Tm)) does not depend on Ra; with given
+            // rates only g beta = Ra nu alpha / ((Th - Tm) H^3) does.
+            const Derived &d = h->d;
+            double dRa = 0.0;
+            if (h->derived_from_Ra) {
+                const double Ra = h->Ra;
+                dRa = a[0] * 3.0 * d.s_nu * d.s_nu * d.nu / (2.0 * Ra) + a[1] * 2.0 * d.s_alpha * d.s_alpha * d.alpha / Ra -
+                      a[2] * p.coef / (2.0 * Ra);
+            } else if (h->Ra > 0.0) {
+                dRa = a[3] * d.gbeta / h->Ra;
+            }
+            const double out[5] = {dRa, a[0], a[1], a[2], a[3]};
+            if (ptr_kind) {
+                if (cudaMemcpy(dL_dparams, out, sizeof out, cudaMemcpyHostToDevice) != cudaSuccess)
+                    st = tape_err(h, LBM_ECUDA, "copy parameters");
+            } else {
+                std::memcpy(dL_dparams, out, sizeof out);
+            }
+        }
+    }
+    // restore the final state
+    lbm_status st2 = move_state(h, fin, 1);
+    h->cur = fin_cur;
+    h->inflight = fin_inflight;
+    h->steps = fin_steps;
+    cudaStreamSynchronize(h->stream);
+    cleanup();
+    return st != LBM_OK ? st : st2;
+}

@@ -44,7 +44,13 @@ struct lbm_melt {
     size_t bytes;
     int timing;
     int bx, by;        // block shape of the per-node kernels (0: default)
+    double Ra;         // as given to create
+    int derived_from_Ra;
+    void *tape;        // recorded run for the adjoint (adjoint.cu)
     std::vector<cudaEvent_t> ev;  // start/stop pairs of timed launches
     size_t ev_used;
     char err[512];
 };
+
+// Release a handle's recorded run (defined with the adjoint).
+void lbm_tape_free(lbm_melt *h);

@@ -174,6 +174,34 @@ __device__ __forceinline__ float pcol(const float (&c)[19], float acc) {
     }
 }
 
+// Sum over ALL rows K.. of parity ODD of mpoly(k, I) c[k] (adjoint use: no
+// row is identically zero there).
+template <int I, int K, bool ODD>
+__device__ __forceinline__ float pcol_all(const float (&c)[19], float acc) {
+    if constexpr (K == 19) {
+        return acc;
+    } else {
+        constexpr int m = mpoly(K, I);
+        if constexpr (m == 0 || row_odd(K) != ODD) return pcol_all<I, K + 1, ODD>(c, acc);
+        else if constexpr (m == 1) return pcol_all<I, K + 1, ODD>(c, acc + c[K]);
+        else if constexpr (m == -1) return pcol_all<I, K + 1, ODD>(c, acc - c[K]);
+        else return pcol_all<I, K + 1, ODD>(c, fmaf((float)m, c[K], acc));
+    }
+}
+
+// out += M^T c over all rows.
+template <int P>
+__device__ __forceinline__ void add_back_pairs_all(float (&out)[19], const float (&c)[19]) {
+    if constexpr (P < 9) {
+        constexpr int i = pf(P), j = opp(pf(P));
+        const float E = pcol_all<i, 0, false>(c, -0.0f);
+        const float O = pcol_all<i, 0, true>(c, -0.0f);
+        out[i] += E + O;
+        out[j] += E - O;
+        add_back_pairs_all<P + 1>(out, c);
+    }
+}
+
 // f += M^T c, pair by pair: f_i += E + O, f_opp(i) += E - O.
 template <int P>
 __device__ __forceinline__ void add_back_pairs(float (&f)[19], const float (&c)[19]) {
@@ -220,6 +248,28 @@ __device__ __forceinline__ float ncol(const float (&c)[7], float acc) {
         else if constexpr (m == 1) return ncol<I, K + 1>(c, acc + c[K]);
         else if constexpr (m == -1) return ncol<I, K + 1>(c, acc - c[K]);
         else return ncol<I, K + 1>(c, fmaf((float)m, c[K], acc));
+    }
+}
+
+// acc + sum over ALL rows k of npoly(k, I) c[k].
+template <int I, int K>
+__device__ __forceinline__ float ncol_all(const float (&c)[7], float acc) {
+    if constexpr (K == 7) {
+        return acc;
+    } else {
+        constexpr int m = npoly(K, I);
+        if constexpr (m == 0) return ncol_all<I, K + 1>(c, acc);
+        else if constexpr (m == 1) return ncol_all<I, K + 1>(c, acc + c[K]);
+        else if constexpr (m == -1) return ncol_all<I, K + 1>(c, acc - c[K]);
+        else return ncol_all<I, K + 1>(c, fmaf((float)m, c[K], acc));
+    }
+}
+
+template <int I>
+__device__ __forceinline__ void add_back7_all(float (&g)[7], const float (&c)[7]) {
+    if constexpr (I < 7) {
+        g[I] = ncol_all<I, 0>(c, g[I]);
+        add_back7_all<I + 1>(g, c);
     }
 }
 

@@ -271,6 +271,8 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     h->face = grid->heated_face;
     h->precision = grid->precision;
     h->Ste = Ste; h->Th = Th; h->Tc = Tc; h->Tm = Tm;
+    h->Ra = Ra;
+    h->derived_from_Ra = rates->derive_from_Ra ? 1 : 0;
     h->stream = (cudaStream_t)cuda_stream;
     KP &p = h->kp;
     p.nx = grid->nx; p.ny = grid->ny; p.nz = grid->nz;
@@ -363,6 +365,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
 LBM_API void lbm_melt_destroy(lbm_melt *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    lbm_tape_free(h);
     free_all(h);
     delete h;
 }
