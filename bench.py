@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--edge", type=int, default=N_EDGE,
                     help="cavity edge (256 is the benchmark workload; smaller edges for profiling captures)")
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the FP16, ensemble and adjoint legs (profiling runs)")
     return ap.parse_args()
 
 
@@ -58,6 +60,19 @@ def dist_setup(n):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_across_ranks(ms, units, dist=None, device="cpu"):
+    """Max of the timed region and sum of the work over ranks (one process
+    per GPU, each advancing its own replica: no data-path collective)."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def hbm_peak():
@@ -195,6 +210,135 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ extra legs
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def precision_leg(steps=200, twin_steps=400):
+    """FP16-storage throughput at 256^3, and the error of FP32 and FP16
+    storage against the FP64 oracle on a 64^3 twin of the workload."""
+    import torch
+    import oracle
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    out = {}
+    cav = Cavity(N_EDGE, N_EDGE, N_EDGE, precision=1, stream=stream.cuda_stream, **CASE)
+    cav.step(10)
+    cav.sync()
+    cav.set_timing(True)
+    cav.kernel_time(reset=True)
+    e0, e1 = _events()
+    e0.record(stream)
+    cav.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k1, nk = cav.kernel_time(reset=True)
+    S = cav.get(T=False, u=False)[2]
+    n_liq, n_sol = liquid_counts(S, cav.H)
+    alg = 104.0 * n_liq + 14.0 * n_sol
+    peak, _ = hbm_peak()
+    out["fp16_mlups"] = n_liq * steps / (ms * 1e-3) / 1e6
+    out["fp16_roofline"] = {"achieved": alg / (k1 / nk * 1e-3) / 1e9, "frac": alg / (k1 / nk * 1e-3) / 1e9 / peak,
+                            "unit": "GB/s", "bytes_per_liquid_node": 104}
+    cav.close()
+    n = 64
+    case = dict(CASE, s0=0.4 * n)
+    o = oracle.Oracle(n, n, n, **case)
+    o.step(twin_steps)
+    To, uo, So, lfo = o.get()
+    o.close()
+    for prec, name in ((0, "fp32"), (1, "fp16")):
+        c = Cavity(n, n, n, precision=prec, stream=stream.cuda_stream, **case)
+        c.step(twin_steps)
+        Tg, ug, Sg, lfg = c.get()
+        c.close()
+        out["%s_twin_error" % name] = {"max_abs_dT": float(np.abs(Tg - To).max()),
+                                       "max_abs_du": float(np.abs(ug - uo).max()),
+                                       "abs_d_liquid_fraction": abs(lfg - lfo)}
+    out["twin"] = "64^3, %d steps from the same initial state, against the FP64 oracle" % twin_steps
+    return out
+
+
+def ensemble_leg(steps=20, n_cav=48, seed=2016):
+    """48 seeded cavities of uneven sizes in one persistent launch per run of
+    steps, against the same cavities stepped one after another."""
+    import torch
+    from paper_1604_03478_gb300 import Ensemble, autotune, inputs
+    stream = torch.cuda.current_stream()
+    draws = inputs.ensemble(n_cav, seed)
+    cases = [dict(nx=d["n"], ny=d["n"], nz=d["n"], face=d["face"], Ra=d["Ra"], Pr=0.02, Ste=d["Ste"], Ma=0.1,
+                  s0=0.4 * d["n"], derive=True) for d in draws]
+    ens = Ensemble(cases, stream=stream.cuda_stream)
+    shape, _ = autotune.tune_ensemble(ens, steps=4)
+    ens.step(4)
+    ens.sync()
+    members = [ens.member(k) for k in range(n_cav)]
+    n_liq = sum(m.totals()["n_liquid"] for m in members)
+    e0, e1 = _events()
+    e0.record(stream)
+    ens.step(steps)
+    e1.record(stream)
+    ens.sync()
+    torch.cuda.synchronize()
+    ms_ens = e0.elapsed_time(e1)
+    e0.record(stream)
+    for m in members:
+        m.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    info = ens.info()
+    ens.close()
+    return {"cavities": n_cav, "nodes": info["nodes"], "liquid_nodes": n_liq, "steps": steps,
+            "mlups": n_liq * steps / (ms_ens * 1e-3) / 1e6, "sequential_mlups": n_liq * steps / (ms_seq * 1e-3) / 1e6,
+            "speedup_vs_sequential": ms_seq / ms_ens, "launch": {"block": shape[0], "nodes_per_thread": shape[1]},
+            "workload": "sizes uniform in {48,64,96,128,160}, Ra log-uniform [1e4,1e6], Ste U[0.05,0.2], "
+                        "Pr 0.02, heated face y0 or z0, seed %d, front at 0.4 H, FP32" % seed}
+
+
+def adjoint_leg(steps=4000, n=96):
+    """Gradient of the final liquid fraction w.r.t. the heated-wall field and
+    Ra on the 96^3 side-heated cube (Ra 1e5, Pr 0.02, Ste 0.1), sqrt(N)
+    checkpoints; times of the plain forward run, the recorded forward and
+    the backward."""
+    import torch
+    from paper_1604_03478_gb300 import Cavity, inputs
+    stream = torch.cuda.current_stream()
+    case = dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
+    wall = (1.0 + inputs.gaussian_field(n * n, 0.01, 5)).astype(np.float32)
+    res = {}
+    for mode in ("plain", "tape"):
+        cav = Cavity(n, n, n, stream=stream.cuda_stream, **case)
+        cav.set_hot_wall(wall)
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        if mode == "plain":
+            cav.step(steps)
+        else:
+            cav.tape_forward(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[mode] = e0.elapsed_time(e1)
+        if mode == "tape":
+            seed = np.full(cav.ncols, 1.0 / (cav.H * cav.ncols))
+            t0 = time.perf_counter()
+            dth, par = cav.tape_backward(seed)
+            res["backward"] = (time.perf_counter() - t0) * 1e3
+            res["dL_dRa"] = par["Ra"]
+            res["grad_norm_wall"] = float(np.linalg.norm(dth))
+        cav.close()
+    return {"cube": n, "steps": steps, "forward_ms": res["plain"], "recorded_forward_ms": res["tape"],
+            "backward_ms": res["backward"], "adjoint_forward_ratio": res["backward"] / res["plain"],
+            "total_over_forward": (res["tape"] + res["backward"]) / res["plain"],
+            "dL_dRa": res["dL_dRa"], "grad_norm_wall": res["grad_norm_wall"],
+            "loss": "final liquid fraction", "checkpoints": "every ceil(sqrt(steps)) steps"}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args):
@@ -240,12 +384,8 @@ def run_gpu(args):
     n_liq1, n_sol1 = liquid_counts(S1, H)
     n_liq = 0.5 * (n_liq0 + n_liq1)
     n_sol = 0.5 * (n_sol0 + n_sol1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * n_liq * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max, units = reduce_across_ranks(ms, n_liq * args.steps, dist, "cuda")
+    value = units / (ms_max * 1e-3) / 1e6
 
     # roofline of the dominant kernel (the fused stream-collide)
     k1_avg_ms = k1_ms / max(k1_n, 1)
@@ -274,17 +414,20 @@ def run_gpu(args):
             raise RuntimeError(L.lbm_melt_last_error(h).decode())
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * n_liq1 * e2e_steps / e2e_s / 1e6
+    e2e_ms, e2e_units = reduce_across_ranks(e2e_s * 1e3, n_liq1 * e2e_steps, dist, "cuda")
+    e2e_value = e2e_units / (e2e_ms * 1e-3) / 1e6
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores = oracle_sample(2, n=n)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": "2 oracle steps of the full %d^3 workload from its initial state (%.1f s)" % (n, dt)}
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.skip_extra and n == N_EDGE and args.precision == 0:
+        extra["precision"] = precision_leg()
+        extra["ensemble"] = ensemble_leg()
+        extra["adjoint"] = adjoint_leg()
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -304,8 +447,9 @@ def run_gpu(args):
                 "d2h_bytes_per_step": ncols * 8 + 8, "steps": e2e_steps},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
-        "all_node_mlups": world * (n ** 3) * args.steps / (ms_max * 1e-3) / 1e6,
+        "all_node_mlups": (units / n_liq) * (n ** 3) / (ms_max * 1e-3) / 1e6,
     }
+    line.update(extra)
     cav.close()
     if rank == 0:
         print(json.dumps(line))
