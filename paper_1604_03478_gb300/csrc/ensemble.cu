@@ -27,11 +27,26 @@
 
 #define LBM_API extern "C" __attribute__((visibility("default")))
 
+// Launch-bound occupancy target of the persistent kernel (blocks of 256
+// per SM) and whether the node variants are out-of-line functions.
+#ifndef LBM_ENS_MINB
+#define LBM_ENS_MINB 2
+#endif
+#ifndef LBM_ENS_NOINLINE
+#define LBM_ENS_NOINLINE 0
+#endif
+#if LBM_ENS_NOINLINE
+#define ENS_FN __device__ __noinline__
+#else
+#define ENS_FN __device__ __forceinline__
+#endif
+
 namespace lbm {
 
 struct CavDesc {
     KP p;
-    int face, cur0, inflight0, pad;
+    int face, cur0, inflight0;
+    int bxs, by, gx, gxy;         // tile: 1 << bxs by by threads; tiles per row and per plane
     void *F, *G;
     int *js[2], *nb[2];
     double *s[2];
@@ -39,12 +54,16 @@ struct CavDesc {
     int *status;
 };
 
+// Everything the launch needs, passed as one __grid_constant__ kernel
+// parameter: the descriptors are read through the constant bank (uniform
+// per block, no aliasing with the distributions being written).
+constexpr int kMaxCavities = 64;
 struct EnsWork {
     int ncav;
     int nodes_per_item;
-    const long long *item_begin;  // ncav + 1 prefix sums of node items
-    const long long *col_begin;   // ncav + 1 prefix sums of column items
-    const CavDesc *desc;
+    long long item_begin[kMaxCavities + 1];  // prefix sums of node items
+    long long col_begin[kMaxCavities + 1];   // prefix sums of column items
+    CavDesc desc[kMaxCavities];
     unsigned int *bar;            // {arrived, generation, timed out}
     long long max_spins;
     int skip_arrival_block;       // fault injection for tests: this block never arrives (-1: none)
@@ -102,82 +121,77 @@ __device__ __forceinline__ int find_cavity(const long long *begin, int n, long l
     return lo;
 }
 
-// Copy descriptor k to shared memory if the block holds another one.
-__device__ __forceinline__ void use_cavity(const EnsWork &w, int k, CavDesc &d, int &dk) {
-    if (dk == k) return;
-    __syncthreads();
-    const int nw = (int)(sizeof(CavDesc) / 4);
-    const unsigned int *src = (const unsigned int *)(w.desc + k);
-    unsigned int *dst = (unsigned int *)&d;
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
-    if (threadIdx.x == 0) dk = k;
-    __syncthreads();
+// One node of phase 1.  Each (face, parity) variant is its own out-of-line
+// function so that the variants do not share one register allocation.
+template <typename ST, int FACE>
+ENS_FN void ens_even(const CavDesc &d, int cur, int x, int y, int z) {
+    even_node<ST, FACE>(d.p, (ST *)d.F, (ST *)d.G, d.js[cur], d.nb[cur], d.gpost, x, y, z);
+}
+template <typename ST, int FACE>
+ENS_FN void ens_odd(const CavDesc &d, int cur, const float *trd, int x, int y, int z) {
+    odd_node<ST, FACE, false>(d.p, nullptr, (ST *)d.F, (ST *)d.G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
+}
+
+// One column of phase 2 (front update) or 3 (flip).
+template <typename ST>
+ENS_FN void ens_column(const CavDesc &d, int cur, int inflight, int phase, int col) {
+    if (phase == 2) {
+        const ST *F = (const ST *)d.F, *G = (const ST *)d.G;
+        if (d.face == 0)
+            front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                inflight, 1, d.status, col);
+        else
+            front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                inflight, 1, d.status, col);
+    } else {
+        ST *F = (ST *)d.F;
+        if (d.face == 0) flip_column<ST, 0>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
+        else flip_column<ST, 1>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
+    }
 }
 
 template <typename ST, int K>
-__global__ void __launch_bounds__(256) k_ensemble(EnsWork w, int nsteps) {
-    __shared__ __align__(16) CavDesc d;
-    __shared__ int dk;
-    if (threadIdx.x == 0) dk = -1;
-    __syncthreads();
+__global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_constant__ EnsWork w, int nsteps) {
     const long long items1 = w.item_begin[w.ncav], items2 = w.col_begin[w.ncav];
     for (int t = 0; t < nsteps; ++t) {
-        // phase 1: fused stream-collide of every node of every cavity
+        // phase 1: fused stream-collide of every node of every cavity; an
+        // item is one (1 << bxs) x by tile of K consecutive z-planes
         for (long long it = blockIdx.x; it < items1; it += gridDim.x) {
             const int k = find_cavity(w.item_begin, w.ncav, it);
-            use_cavity(w, k, d, dk);
+            const CavDesc &d = w.desc[k];
             const int cur = d.cur0 ^ (t & 1), odd = d.inflight0 ^ (t & 1);
             const float *trd = t == 0 ? d.thw_rd0 : d.thw;
-            const long long base = (it - w.item_begin[k]) * (long long)w.nodes_per_item;
-            const long long nxy = (long long)d.p.nx * d.p.ny;
+            const int li = (int)(it - w.item_begin[k]);
+            const int zc = li / d.gxy, r = li - zc * d.gxy;
+            const int iy = r / d.gx, ix = r - iy * d.gx;
+            const int x = (ix << d.bxs) + (threadIdx.x & ((1 << d.bxs) - 1));
+            const int y = iy * d.by + (threadIdx.x >> d.bxs);
+            if (x >= d.p.nx || y >= d.p.ny) continue;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const long long c = base + threadIdx.x + (long long)j * blockDim.x;
-                if (c >= d.p.N) continue;
-                const int z = (int)(c / nxy);
-                const int rem = (int)(c - z * nxy);
-                const int y = rem / d.p.nx, x = rem - y * d.p.nx;
-                ST *F = (ST *)d.F, *G = (ST *)d.G;
+                const int z = zc * K + j;
+                if (z >= d.p.nz) break;
                 if (d.face == 0) {
-                    if (odd) odd_node<ST, 0>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
-                    else even_node<ST, 0>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, x, y, z);
+                    if (odd) ens_odd<ST, 0>(d, cur, trd, x, y, z);
+                    else ens_even<ST, 0>(d, cur, x, y, z);
                 } else {
-                    if (odd) odd_node<ST, 1>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
-                    else even_node<ST, 1>(d.p, F, G, d.js[cur], d.nb[cur], d.gpost, x, y, z);
+                    if (odd) ens_odd<ST, 1>(d, cur, trd, x, y, z);
+                    else ens_even<ST, 1>(d, cur, x, y, z);
                 }
             }
         }
         if (!grid_barrier(w, gridDim.x)) return;
-        // phase 2: front update (Eq. 6) of every column
-        for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
-            const int k = find_cavity(w.col_begin, w.ncav, it);
-            use_cavity(w, k, d, dk);
-            const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
-            const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
-            if (col < d.p.ncols) {
-                const ST *F = (const ST *)d.F, *G = (const ST *)d.G;
-                if (d.face == 0)
-                    front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
-                                        inflight, 1, d.status, col);
-                else
-                    front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
-                                        inflight, 1, d.status, col);
+        // phases 2 and 3: front update (Eq. 6), then flip, of every column
+        for (int phase = 2; phase <= 3; ++phase) {
+            for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
+                const int k = find_cavity(w.col_begin, w.ncav, it);
+                const CavDesc &d = w.desc[k];
+                const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
+                const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
+                if (col < d.p.ncols) ens_column<ST>(d, cur, inflight, phase, col);
             }
+            if (!grid_barrier(w, gridDim.x)) return;
         }
-        if (!grid_barrier(w, gridDim.x)) return;
-        // phase 3: phase flip and the 3x3 liquid-count bounds
-        for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
-            const int k = find_cavity(w.col_begin, w.ncav, it);
-            use_cavity(w, k, d, dk);
-            const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
-            const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
-            if (col < d.p.ncols) {
-                ST *F = (ST *)d.F;
-                if (d.face == 0) flip_column<ST, 0>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
-                else flip_column<ST, 1>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
-            }
-        }
-        if (!grid_barrier(w, gridDim.x)) return;
     }
 }
 
@@ -195,9 +209,8 @@ struct lbm_ensemble {
     int precision;
     int block, K, grid;
     long long max_spins;
-    CavDesc *desc_dev;
-    long long *item_dev, *col_dev;
     unsigned int *bar_dev;
+    long long items[lbm::kMaxCavities + 1], cols[lbm::kMaxCavities + 1];
     std::vector<CavDesc> desc;
     cudaGraphExec_t graph;
     int graph_steps;
@@ -236,8 +249,21 @@ const void *kernel_ptr(int precision, int K) {
     return (const void *)lbm::k_ensemble<float, 4>;
 }
 
-void fill_desc(lbm_melt *h, CavDesc &d) {
+// Tile of a cavity for the block size: as wide along x as the row needs (a
+// power of two, at least 32), the rest of the block along y.
+void tile(const lbm::KP &p, int block, int &bxs, int &by) {
+    int bx = 32;
+    while (bx < p.nx && bx < block) bx *= 2;
+    bxs = 0;
+    while ((1 << bxs) < bx) ++bxs;
+    by = block / bx;
+}
+
+void fill_desc(lbm_melt *h, CavDesc &d, int block) {
     std::memset(&d, 0, sizeof d);
+    tile(h->kp, block, d.bxs, d.by);
+    d.gx = (h->kp.nx + (1 << d.bxs) - 1) >> d.bxs;
+    d.gxy = d.gx * ((h->kp.ny + d.by - 1) / d.by);
     d.p = h->kp;
     d.face = h->face;
     d.cur0 = h->cur;
@@ -253,21 +279,23 @@ void fill_desc(lbm_melt *h, CavDesc &d) {
 
 // Work-list prefix sums and the co-resident grid for the launch shape.
 lbm_status plan(lbm_ensemble *e) {
-    std::vector<long long> items(e->n + 1, 0), cols(e->n + 1, 0);
-    const long long per = (long long)e->block * e->K;
+    e->items[0] = e->cols[0] = 0;
     for (int k = 0; k < e->n; ++k) {
-        items[k + 1] = items[k] + (e->cav[k]->kp.N + per - 1) / per;
-        cols[k + 1] = cols[k] + (e->cav[k]->kp.ncols + e->block - 1) / e->block;
+        const lbm::KP &p = e->cav[k]->kp;
+        int bxs, by;
+        tile(p, e->block, bxs, by);
+        const long long gx = (p.nx + (1 << bxs) - 1) >> bxs, gy = (p.ny + by - 1) / by;
+        const long long gz = (p.nz + e->K - 1) / e->K;
+        e->items[k + 1] = e->items[k] + gx * gy * gz;
+        e->cols[k + 1] = e->cols[k] + (p.ncols + e->block - 1) / e->block;
     }
-    ECK(cudaMemcpyAsync(e->item_dev, items.data(), items.size() * 8, cudaMemcpyHostToDevice, e->stream), "plan");
-    ECK(cudaMemcpyAsync(e->col_dev, cols.data(), cols.size() * 8, cudaMemcpyHostToDevice, e->stream), "plan");
     int dev = 0, sms = 0, per_sm = 0;
     ECK(cudaGetDevice(&dev), "device");
     ECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     ECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr(e->precision, e->K), e->block, 0),
         "occupancy");
     if (per_sm < 1) return ens_err(e, LBM_EINVAL, "block size %d does not fit on an SM", e->block);
-    e->grid = (int)std::min<long long>((long long)per_sm * sms, std::max(items[e->n], cols[e->n]));
+    e->grid = (int)std::min<long long>((long long)per_sm * sms, std::max(e->items[e->n], e->cols[e->n]));
     if (e->graph) {
         cudaGraphExecDestroy(e->graph);
         e->graph = nullptr;
@@ -275,24 +303,30 @@ lbm_status plan(lbm_ensemble *e) {
     return LBM_OK;
 }
 
-lbm_status upload_desc(lbm_ensemble *e) {
-    for (int k = 0; k < e->n; ++k) fill_desc(e->cav[k], e->desc[k]);
-    ECK(cudaMemcpyAsync(e->desc_dev, e->desc.data(), e->desc.size() * sizeof(CavDesc), cudaMemcpyHostToDevice,
-                        e->stream), "descriptors");
-    return LBM_OK;
+// Descriptors from the members' current phases; a change invalidates the
+// captured graph (its kernel parameters hold the descriptors by value).
+void refresh_desc(lbm_ensemble *e) {
+    for (int k = 0; k < e->n; ++k) fill_desc(e->cav[k], e->desc[k], e->block);
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
 }
 
 lbm_status launch(lbm_ensemble *e, int nsteps, int skip_block) {
-    EnsWork w;
-    w.ncav = e->n;
-    w.nodes_per_item = e->block * e->K;
-    w.item_begin = e->item_dev;
-    w.col_begin = e->col_dev;
-    w.desc = e->desc_dev;
-    w.bar = e->bar_dev;
-    w.max_spins = e->max_spins;
-    w.skip_arrival_block = skip_block;
-    void *args[] = {&w, &nsteps};
+    EnsWork *w = new (std::nothrow) EnsWork();
+    if (!w) return LBM_ENOMEM;
+    w->ncav = e->n;
+    w->nodes_per_item = e->block * e->K;
+    for (int k = 0; k <= e->n; ++k) {
+        w->item_begin[k] = e->items[k];
+        w->col_begin[k] = e->cols[k];
+    }
+    for (int k = 0; k < e->n; ++k) w->desc[k] = e->desc[k];
+    w->bar = e->bar_dev;
+    w->max_spins = e->max_spins;
+    w->skip_arrival_block = skip_block;
+    void *args[] = {w, &nsteps};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(e->grid);
     cfg.blockDim = dim3(e->block);
@@ -302,8 +336,10 @@ lbm_status launch(lbm_ensemble *e, int nsteps, int skip_block) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    ECK(cudaMemsetAsync(e->bar_dev, 0, 3 * sizeof(unsigned int), e->stream), "barrier reset");
-    ECK(cudaLaunchKernelExC(&cfg, kernel_ptr(e->precision, e->K), args), "ensemble launch");
+    cudaError_t err = cudaMemsetAsync(e->bar_dev, 0, 3 * sizeof(unsigned int), e->stream);
+    if (err == cudaSuccess) err = cudaLaunchKernelExC(&cfg, kernel_ptr(e->precision, e->K), args);
+    delete w;
+    ECK(err, "ensemble launch");
     return LBM_OK;
 }
 
@@ -330,7 +366,7 @@ bool desc_current(lbm_ensemble *e) {
 }  // namespace
 
 LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *cuda_stream, lbm_ensemble **out) {
-    if (!out || n < 1 || !cases) return LBM_EINVAL;
+    if (!out || n < 1 || n > lbm::kMaxCavities || !cases) return LBM_EINVAL;
     *out = nullptr;
     lbm_ensemble *e = new (std::nothrow) lbm_ensemble();
     if (!e) return LBM_ENOMEM;
@@ -343,7 +379,7 @@ LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *
     e->desc.resize(n);
     auto fail = [&](lbm_status st) {
         for (lbm_melt *h : e->cav) lbm_melt_destroy(h);
-        cudaFree(e->desc_dev); cudaFree(e->item_dev); cudaFree(e->col_dev); cudaFree(e->bar_dev);
+        cudaFree(e->bar_dev);
         if (e->ev_in) cudaEventDestroy(e->ev_in);
         if (e->ev_out) cudaEventDestroy(e->ev_out);
         if (e->stream) cudaStreamDestroy(e->stream);
@@ -366,11 +402,9 @@ LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *
         if (k == 0) e->precision = h->precision;
         else if (h->precision != e->precision) return fail(LBM_EINVAL);
     }
-    if (cudaMalloc(&e->desc_dev, n * sizeof(CavDesc)) != cudaSuccess ||
-        cudaMalloc(&e->item_dev, (n + 1) * 8) != cudaSuccess || cudaMalloc(&e->col_dev, (n + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&e->bar_dev, 4 * sizeof(unsigned int)) != cudaSuccess)
-        return fail(LBM_ENOMEM);
-    if (plan(e) != LBM_OK || upload_desc(e) != LBM_OK) return fail(LBM_ECUDA);
+    if (cudaMalloc(&e->bar_dev, 4 * sizeof(unsigned int)) != cudaSuccess) return fail(LBM_ENOMEM);
+    refresh_desc(e);
+    if (plan(e) != LBM_OK) return fail(LBM_ECUDA);
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) return fail(LBM_ECUDA);
     *out = e;
     return LBM_OK;
@@ -381,9 +415,6 @@ LBM_API void lbm_ensemble_destroy(lbm_ensemble *e) {
     cudaStreamSynchronize(e->stream);
     if (e->graph) cudaGraphExecDestroy(e->graph);
     for (lbm_melt *h : e->cav) lbm_melt_destroy(h);
-    cudaFree(e->desc_dev);
-    cudaFree(e->item_dev);
-    cudaFree(e->col_dev);
     cudaFree(e->bar_dev);
     cudaEventDestroy(e->ev_in);
     cudaEventDestroy(e->ev_out);
@@ -395,14 +426,15 @@ LBM_API const char *lbm_ensemble_last_error(const lbm_ensemble *e) { return e ? 
 
 LBM_API lbm_status lbm_ensemble_set_launch(lbm_ensemble *e, int block, int nodes_per_thread, int graph_steps) {
     if (!e) return LBM_EINVAL;
-    if (block < 32 || block > 256 || block % 32)
-        return ens_err(e, LBM_EINVAL, "block must be a multiple of 32 in [32, 256]");
+    if (block != 64 && block != 128 && block != 256)
+        return ens_err(e, LBM_EINVAL, "block must be 64, 128 or 256");
     if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4)
         return ens_err(e, LBM_EINVAL, "nodes_per_thread must be 1, 2 or 4");
     if (graph_steps < 2 || (graph_steps & 1)) return ens_err(e, LBM_EINVAL, "graph_steps must be even and >= 2");
     e->block = block;
     e->K = nodes_per_thread;
     e->graph_steps = graph_steps;
+    refresh_desc(e);
     lbm_status st = plan(e);
     if (st == LBM_OK) ECK(cudaStreamSynchronize(e->stream), "synchronize");
     return st;
@@ -425,10 +457,7 @@ LBM_API lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps) {
     // work after this
     ECK(cudaEventRecord(e->ev_in, e->user), "event");
     ECK(cudaStreamWaitEvent(e->stream, e->ev_in, 0), "wait");
-    if (!desc_current(e)) {
-        lbm_status st = upload_desc(e);
-        if (st != LBM_OK) return st;
-    }
+    if (!desc_current(e)) refresh_desc(e);
     long long left = nsteps;
     const long long G = e->graph_steps;
     if (left >= G) {
@@ -455,6 +484,7 @@ LBM_API lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps) {
         if (st != LBM_OK) return st;
     }
     advance_handles(e, nsteps);
+    if (left & 1) refresh_desc(e);  // the members' phases moved on
     ECK(cudaEventRecord(e->ev_out, e->stream), "event");
     ECK(cudaStreamWaitEvent(e->user, e->ev_out, 0), "wait");
     return LBM_OK;
@@ -465,13 +495,11 @@ LBM_API lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps) {
 // LBM_ETIMEOUT.  The ensemble's state is not meaningful afterwards.
 LBM_API lbm_status lbm_ensemble_inject_barrier_fault(lbm_ensemble *e, int block) {
     if (!e || block < 0 || block >= e->grid) return LBM_EINVAL;
-    if (!desc_current(e)) {
-        lbm_status st = upload_desc(e);
-        if (st != LBM_OK) return st;
-    }
+    if (!desc_current(e)) refresh_desc(e);
     lbm_status st = launch(e, 1, block);
     if (st != LBM_OK) return st;
     advance_handles(e, 1);
+    refresh_desc(e);
     return LBM_OK;
 }
 

@@ -19,6 +19,7 @@ struct Derived {
 
 struct lbm_melt {
     lbm::KP kp;
+    lbm::Links lk;     // interior link offsets of the odd step
     Derived d;
     int face, precision;
     double Ste, Th, Tc, Tm;

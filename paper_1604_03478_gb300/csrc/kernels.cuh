@@ -36,6 +36,21 @@ template <int FACE> __device__ __forceinline__ long long off7(const KP &p, int i
     return (long long)tx(i) + (long long)ty(i) * p.nx + (long long)tz(i) * p.nx * p.ny;
 }
 
+// Element offsets of the odd step's interior links: from the table lk (a
+// kernel parameter) when TAB, else from the extents.
+template <int FACE, bool TAB> __device__ __forceinline__ long long fin_off(const KP &p, const Links *lk, int i) {
+    return TAB ? lk->fin[i] : opp(i) * p.ld - off19<FACE>(p, i);
+}
+template <int FACE, bool TAB> __device__ __forceinline__ long long fout_off(const KP &p, const Links *lk, int i) {
+    return TAB ? lk->fout[i] : i * p.ld + off19<FACE>(p, i);
+}
+template <int FACE, bool TAB> __device__ __forceinline__ long long gin_off(const KP &p, const Links *lk, int i) {
+    return TAB ? lk->gin[i] : opp7(i) * p.ld - off7<FACE>(p, i);
+}
+template <int FACE, bool TAB> __device__ __forceinline__ long long gout_off(const KP &p, const Links *lk, int i) {
+    return TAB ? lk->gout[i] : i * p.ld + off7<FACE>(p, i);
+}
+
 // Post-collision shifted g of a solid node: the ghost node (first solid node
 // of its column) takes the populations prepared by k_front; deeper nodes are
 // at rest at Tm, i.e. zero.
@@ -122,8 +137,11 @@ __device__ __forceinline__ float wall_value(const KP &p, int dir, float v, float
     return w == 3 ? v : -v + 2.0f * w7(dir) * ((w == 1 ? Th_col : p.Tc) - p.Tm);
 }
 
-template <typename ST, int FACE>
-__device__ __forceinline__ void odd_node(const KP &p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
+// TAB: take the interior link offsets from the precomputed tables of KP
+// (kernel parameters: constant-bank operands); false computes them from the
+// extents, which keeps them out of registers when KP lives in shared memory.
+template <typename ST, int FACE, bool TAB = true>
+__device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
                                          const int *__restrict__ nb, const float *__restrict__ gpost,
                                          const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
                                          int y, int z) {
@@ -145,9 +163,9 @@ __device__ __forceinline__ void odd_node(const KP &p, ST *__restrict__ F, ST *__
         unsigned lm = 0x7fffeu, im = 0x7eu;
         if (interior) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(Fc + p.fin[i]);
+            for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(Fc + fin_off<FACE, TAB>(p, lk, i));
 #pragma unroll
-            for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(Gc + p.gin[i]);
+            for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(Gc + gin_off<FACE, TAB>(p, lk, i));
         } else {
             lm = link_mask<FACE>(p, js, x, y, z);
             im = inside_mask(p, x, y, z);
@@ -155,27 +173,27 @@ __device__ __forceinline__ void odd_node(const KP &p, ST *__restrict__ F, ST *__
             f[0] = Store<ST>::ld(Fc);
 #pragma unroll
             for (int i = 1; i < 19; ++i)  // else bounce-back: f*_opp(i) parked in slot i
-                f[i] = Store<ST>::ld(((lm >> i) & 1u) ? Fc + p.fin[i] : Fc + i * p.ld);
+                f[i] = Store<ST>::ld(((lm >> i) & 1u) ? Fc + fin_off<FACE, TAB>(p, lk, i) : Fc + i * p.ld);
             g[0] = Store<ST>::ld(Gc);
 #pragma unroll
             for (int i = 1; i < 7; ++i) {
                 const bool in = (im >> i) & 1u;
-                const float v = Store<ST>::ld(in ? Gc + p.gin[i] : Gc + i * p.ld);
+                const float v = Store<ST>::ld(in ? Gc + gin_off<FACE, TAB>(p, lk, i) : Gc + i * p.ld);
                 g[i] = in ? v : wall_value<FACE>(p, opp7(i), v, th_rd);
             }
         }
         collide(p, f, g);
         if (interior) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) Store<ST>::st(Fc + p.fout[i], f[i]);
+            for (int i = 0; i < 19; ++i) Store<ST>::st(Fc + fout_off<FACE, TAB>(p, lk, i), f[i]);
 #pragma unroll
-            for (int i = 0; i < 7; ++i) Store<ST>::st(Gc + p.gout[i], g[i]);
+            for (int i = 0; i < 7; ++i) Store<ST>::st(Gc + gout_off<FACE, TAB>(p, lk, i), g[i]);
             return;
         }
         Store<ST>::st(Fc, f[0]);
 #pragma unroll
         for (int i = 1; i < 19; ++i)
-            Store<ST>::st(((lm >> opp(i)) & 1u) ? Fc + p.fout[i] : Fc + opp(i) * p.ld, f[i]);
+            Store<ST>::st(((lm >> opp(i)) & 1u) ? Fc + fout_off<FACE, TAB>(p, lk, i) : Fc + opp(i) * p.ld, f[i]);
     } else {
         if (deep_solid(p, a, nbv)) return;
         solid_post(p, a == jsc, gpost, col, g);
@@ -186,7 +204,8 @@ __device__ __forceinline__ void odd_node(const KP &p, ST *__restrict__ F, ST *__
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
         const bool out = (im >> opp7(i)) & 1u;
-        Store<ST>::st(out ? Gc + p.gout[i] : Gc + opp7(i) * p.ld, out ? g[i] : wall_value<FACE>(p, i, g[i], th_wr));
+        Store<ST>::st(out ? Gc + gout_off<FACE, TAB>(p, lk, i) : Gc + opp7(i) * p.ld,
+                      out ? g[i] : wall_value<FACE>(p, i, g[i], th_wr));
     }
 }
 
@@ -194,12 +213,12 @@ template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__restrict__ G,
                                              const int *__restrict__ js, const int *__restrict__ nb,
                                              const float *__restrict__ gpost, const float *__restrict__ thw_rd,
-                                             const float *__restrict__ thw_wr) {
+                                             const float *__restrict__ thw_wr, const __grid_constant__ Links lk) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
-    odd_node<ST, FACE>(p, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+    odd_node<ST, FACE>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
 }
 
 

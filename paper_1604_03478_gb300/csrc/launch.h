@@ -19,6 +19,7 @@ struct Bufs {
     float *gpost;                // ghost-node post-collision g, 7 x ncols
     const float *thw_rd, *thw_wr;
     int *status;
+    const Links *lk;             // interior link offsets of the odd step
 };
 
 template <typename ST> struct Launch {

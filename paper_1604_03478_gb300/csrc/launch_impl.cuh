@@ -12,10 +12,10 @@ cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Buf
     dim3 grd = node_grid(p, blk);
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr);
+        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk);
         else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
     } else {
-        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr);
+        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk);
         else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
     }
     return cudaGetLastError();

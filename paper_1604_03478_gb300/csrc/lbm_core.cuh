@@ -106,8 +106,13 @@ struct KP {
     double Tm_d, Th_d;
     double coef;      // alpha Ste / (Th - Tm): Eq. 6 front speed per unit -dT/da
     int skip_deep;    // Tc == Tm: deep solid nodes need no update
-    // element offsets of the interior odd step, relative to node c:
-    // f_i is pulled from slot opp(i) of c - e_i and pushed to slot i of c + e_i
+};
+
+// Element offsets of the interior odd step, relative to node c: f_i is
+// pulled from slot opp(i) of c - e_i and pushed to slot i of c + e_i (g
+// likewise).  Passed as a kernel parameter so that they are constant-bank
+// operands.
+struct Links {
     long long fin[19], fout[19], gin[7], gout[7];
 };
 

@@ -150,6 +150,7 @@ Bufs bufs(lbm_melt *h) {
     b.thw_rd = h->thw_pending ? h->thw_prev : h->thw_cur;
     b.thw_wr = h->thw_cur;
     b.status = h->status_dev;
+    b.lk = &h->lk;
     return b;
 }
 
@@ -290,13 +291,13 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         const long long sy = p.nx, sz = (long long)p.nx * p.ny;
         for (int i = 0; i < 19; ++i) {
             const long long off = lbm::ex(i) + lbm::ey(i) * sy + lbm::ez(i) * sz;
-            p.fin[i] = lbm::opp(i) * p.ld - off;
-            p.fout[i] = i * p.ld + off;
+            h->lk.fin[i] = lbm::opp(i) * p.ld - off;
+            h->lk.fout[i] = i * p.ld + off;
         }
         for (int i = 0; i < 7; ++i) {
             const long long off = lbm::tx(i) + lbm::ty(i) * sy + lbm::tz(i) * sz;
-            p.gin[i] = lbm::opp7(i) * p.ld - off;
-            p.gout[i] = i * p.ld + off;
+            h->lk.gin[i] = lbm::opp7(i) * p.ld - off;
+            h->lk.gout[i] = i * p.ld + off;
         }
     }
     auto fail = [&](lbm_status s) { free_all(h); delete h; return s; };
