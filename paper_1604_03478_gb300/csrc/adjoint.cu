@@ -39,17 +39,30 @@ namespace lbm {
 
 // -------------------------------------------------------------- snapshot
 // Natural shifted state of one time level: fh (19 x N, zero at solid nodes)
-// then gh (7 x N), FP32.
+// then gh (7 x N), FP32, with copies of the fronts s, the liquid counts and
+// their 3x3 ranges.  Nodes two or more above the largest liquid count of
+// their 3x3 neighbour columns are not written: the reverse sweep reads the
+// snapshot of a level only below the liquid count of that level or of the
+// level before, which differ by at most one.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_snapshot(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
-                                                  const int *__restrict__ js, const float *__restrict__ thw,
-                                                  int inflight, float *__restrict__ out) {
+__global__ void __launch_bounds__(128) k_snapshot(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+                                                  const int *__restrict__ js, const int *__restrict__ nb,
+                                                  const double *__restrict__ s, const float *__restrict__ thw,
+                                                  int inflight, float *__restrict__ out, double *__restrict__ out_s,
+                                                  int *__restrict__ out_js, int *__restrict__ out_nb) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
+    const int nbv = nb[col];
+    if (a == 0) {  // the column's front, liquid count and neighbourhood range
+        out_s[col] = s[col];
+        out_js[col] = js[col];
+        out_nb[col] = nbv;
+    }
+    if (a >= (nbv & 0xffff) + 2) return;
     float g[7], f[19];
     gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
     const bool liq = a < js[col];
@@ -179,7 +192,7 @@ __device__ __forceinline__ double snap_T(const KP &p, const float *snap, int col
 // nodes' temperature adjoint added to lam1 (adjoint of the state at t+1),
 // the wall field, and d/d coef.
 template <int FACE>
-__global__ void __launch_bounds__(128) k_adj_front(KP p, const float *__restrict__ snap1, const double *__restrict__ s,
+__global__ void __launch_bounds__(128) k_adj_front(const __grid_constant__ KP p, const float *__restrict__ snap1, const double *__restrict__ s,
                                                    const float *__restrict__ thw, const double *__restrict__ lams1,
                                                    double *__restrict__ lams0, double *__restrict__ wp,
                                                    double *__restrict__ wq, float *__restrict__ lam1,
@@ -238,11 +251,9 @@ __global__ void __launch_bounds__(128) k_adj_front(KP p, const float *__restrict
 }
 
 // The slopes s_p, s_q of column c' read the fronts of its neighbours (with a
-// mirror at the side walls); gather their d/d s back to each column.
-__global__ void __launch_bounds__(128) k_adj_slopes(KP p, const double *__restrict__ wp,
-                                                    const double *__restrict__ wq, double *__restrict__ lams0) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= p.ncols) return;
+// mirror at the side walls); the sum of their d/d s for column col.
+__device__ __forceinline__ double slope_terms(const KP &p, const double *__restrict__ wp,
+                                              const double *__restrict__ wq, int col) {
     const int P1 = p.P1, P2 = p.P2;
     const int pp = col % P1, q = col / P1;
     double acc = 0.0;
@@ -258,15 +269,23 @@ __global__ void __launch_bounds__(128) k_adj_slopes(KP p, const double *__restri
         if (q == 0) acc -= 0.5 * wq[col];
         if (q == P2 - 1) acc += 0.5 * wq[col];
     }
-    lams0[col] += acc;
+    return acc;
 }
 
 // ----------------------------------------- streaming and collision, reversed
+// The adjoint of a solid node other than the ghost node is zero.  Nodes three
+// or more above the largest liquid count of their 3x3 neighbour columns are
+// not written: the buffer already holds zero there.  It was zeroed before the
+// sweep and then holds the adjoint of two levels later (or zero, by the same
+// argument), which is nonzero only up to the liquid count of that level
+// (ghost node) or one above the count of the level between (front terms);
+// liquid counts change by at most one per step (|ds| <= 1/2, else the run
+// stops as unstable), so both bounds lie below the skipped nodes.
 template <int FACE>
-__global__ void __launch_bounds__(128) k_adj_node(KP p, const float *__restrict__ snap, const int *__restrict__ js,
-                                                  const float *__restrict__ lam1, float *__restrict__ lam0,
-                                                  float *__restrict__ lgpost, double *__restrict__ lthw,
-                                                  double *__restrict__ part) {
+__global__ void __launch_bounds__(128) k_adj_node(const __grid_constant__ KP p, const float *__restrict__ snap, const int *__restrict__ js,
+                                                  const int *__restrict__ nb, const float *__restrict__ lam1,
+                                                  float *__restrict__ lam0, float *__restrict__ lgpost,
+                                                  double *__restrict__ lthw, double *__restrict__ part) {
     __shared__ double sh[3][128];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -285,8 +304,10 @@ __global__ void __launch_bounds__(128) k_adj_node(KP p, const float *__restrict_
             lthw[col] += 2.0 * (double)w7(iin) * (double)lam1[(19 + iin) * N + c];
         }
         if (a > jsc) {
+            if (a < (nb[col] & 0xffff) + 3) {
 #pragma unroll
-            for (int i = 0; i < 26; ++i) lam0[i * N + c] = 0.0f;
+                for (int i = 0; i < 26; ++i) lam0[i * N + c] = 0.0f;
+            }
         } else {
             // g*: every node streams g; the transpose of the pull is a gather
             float lg[7];
@@ -349,14 +370,17 @@ __global__ void __launch_bounds__(128) k_adj_node(KP p, const float *__restrict_
 // ---------------------------------------------- ghost populations, reversed
 // g*_ghost = w (T_ghost - Tm) + N^T D^-1 (I - Q)(n_L - n^eq_L), with T_ghost
 // on the line through (s, Tm) and the guarded node (or the wall).
+// Also gathers the slope terms of Eq. 6 into lambda_s (k_adj_slopes).
 template <int FACE>
-__global__ void __launch_bounds__(128) k_adj_ghost(KP p, const float *__restrict__ snap, const int *__restrict__ js,
+__global__ void __launch_bounds__(128) k_adj_ghost(const __grid_constant__ KP p, const float *__restrict__ snap, const int *__restrict__ js,
                                                    const double *__restrict__ s, const float *__restrict__ thw,
                                                    const float *__restrict__ lgpost, float *__restrict__ lam0,
                                                    double *__restrict__ lams0, double *__restrict__ lthw,
-                                                   double *__restrict__ lsal, double *__restrict__ lgb) {
+                                                   double *__restrict__ lsal, double *__restrict__ lgb,
+                                                   const double *__restrict__ wp, const double *__restrict__ wq) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= p.ncols) return;
+    lams0[col] += slope_terms(p, wp, wq, col);
     const int H = p.H, jn = js[col];
     if (jn >= H) return;
     const long long N = p.N;
@@ -556,6 +580,11 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     if (!h || !seed) return LBM_EINVAL;
     lbm_tape *t = (lbm_tape *)h->tape;
     if (!t) return tape_err(h, LBM_EINVAL, "no recorded run (call lbm_melt_tape_forward first)");
+    // the sweep relies on fronts that move at most half a node per step
+    {
+        const lbm_status s0 = lbm_check_status(h);
+        if (s0 != LBM_OK) return s0;
+    }
     const lbm::KP &p = h->kp;
     const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
     const long long C = t->C;
@@ -567,10 +596,11 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     float *snap = nullptr, *lam[2] = {nullptr, nullptr}, *lgpost = nullptr;
     double *snap_s = nullptr, *lams[2] = {nullptr, nullptr}, *wp = nullptr, *wq = nullptr, *lthw = nullptr;
     double *part = nullptr, *lsal = nullptr, *lgb = nullptr, *lcoef = nullptr, *acc = nullptr;
-    int *snap_js = nullptr;
+    int *snap_js = nullptr, *snap_nb = nullptr;
     struct Alloc { void **p; size_t b; } al[] = {
         {(void **)&fin, t->ck_bytes}, {(void **)&snap, (size_t)(C + 1) * 26 * N * 4},
         {(void **)&snap_s, (size_t)(C + 1) * nc * 8}, {(void **)&snap_js, (size_t)(C + 1) * nc * 4},
+        {(void **)&snap_nb, (size_t)(C + 1) * nc * 4},
         {(void **)&lam[0], 26 * N * 4}, {(void **)&lam[1], 26 * N * 4}, {(void **)&lgpost, 7 * nc * 4},
         {(void **)&lams[0], nc * 8}, {(void **)&lams[1], nc * 8}, {(void **)&wp, nc * 8}, {(void **)&wq, nc * 8},
         {(void **)&lthw, nc * 8}, {(void **)&part, nblk * 3 * 8}, {(void **)&lsal, nc * 8},
@@ -609,15 +639,13 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         const float *thw = h->thw_cur;
         float *out = snap + (size_t)j * 26 * N;
         if (h->precision == 1) {
-            if (h->face == 0) lbm::k_snapshot<__half, 0><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, thw, h->inflight, out);
-            else lbm::k_snapshot<__half, 1><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, thw, h->inflight, out);
+            if (h->face == 0) lbm::k_snapshot<__half, 0><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
+            else lbm::k_snapshot<__half, 1><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
         } else {
-            if (h->face == 0) lbm::k_snapshot<float, 0><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, thw, h->inflight, out);
-            else lbm::k_snapshot<float, 1><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, thw, h->inflight, out);
+            if (h->face == 0) lbm::k_snapshot<float, 0><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
+            else lbm::k_snapshot<float, 1><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
         }
         TCK(cudaGetLastError(), "snapshot");
-        TCK(cudaMemcpyAsync(snap_s + (size_t)j * nc, h->s[h->cur], nc * 8, cudaMemcpyDeviceToDevice, h->stream), "snap s");
-        TCK(cudaMemcpyAsync(snap_js + (size_t)j * nc, h->js[h->cur], nc * 4, cudaMemcpyDeviceToDevice, h->stream), "snap js");
         return LBM_OK;
     };
     const float *thw = h->thw_cur;
@@ -637,16 +665,15 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             const float *s1 = snap + (size_t)(j + 1) * 26 * N, *s0 = snap + (size_t)j * 26 * N;
             const double *st_s = snap_s + (size_t)j * nc;
             const int *st_js = snap_js + (size_t)j * nc;
+            const int *st_nb = snap_nb + (size_t)j * nc;
             if (h->face == 0) {
                 lbm::k_adj_front<0><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
-                lbm::k_adj_slopes<<<cgrid, 128, 0, h->stream>>>(p, wp, wq, lams[0]);
-                lbm::k_adj_node<0><<<grd, blk, 0, h->stream>>>(p, s0, st_js, lam[1], lam[0], lgpost, lthw, part);
-                lbm::k_adj_ghost<0><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb);
+                lbm::k_adj_node<0><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
+                lbm::k_adj_ghost<0><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp, wq);
             } else {
                 lbm::k_adj_front<1><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
-                lbm::k_adj_slopes<<<cgrid, 128, 0, h->stream>>>(p, wp, wq, lams[0]);
-                lbm::k_adj_node<1><<<grd, blk, 0, h->stream>>>(p, s0, st_js, lam[1], lam[0], lgpost, lthw, part);
-                lbm::k_adj_ghost<1><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb);
+                lbm::k_adj_node<1><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
+                lbm::k_adj_ghost<1><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp, wq);
             }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { st = tape_err(h, LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e)); break; }

@@ -55,3 +55,7 @@ struct lbm_melt {
 
 // Release a handle's recorded run (defined with the adjoint).
 void lbm_tape_free(lbm_melt *h);
+// Reads the sticky front status on the handle's stream (synchronises):
+// LBM_EUNSTABLE after a step with |ds| > 1/2, LBM_ENAN after a non-finite
+// front temperature, else LBM_OK.
+lbm_status lbm_check_status(lbm_melt *h);

@@ -96,7 +96,7 @@ __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *_
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_even(KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const int *__restrict__ nb,
                                               const float *__restrict__ gpost) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,7 +210,7 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_odd(KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_odd(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                              const int *__restrict__ js, const int *__restrict__ nb,
                                              const float *__restrict__ gpost, const float *__restrict__ thw_rd,
                                              const float *__restrict__ thw_wr, const __grid_constant__ Links lk) {
@@ -384,7 +384,7 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_front(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_front(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                const int *__restrict__ js, int *__restrict__ js_next,
                                                const double *__restrict__ s, double *__restrict__ s_next,
                                                float *__restrict__ gpost, const float *__restrict__ thw,
@@ -465,7 +465,7 @@ __device__ __forceinline__ void flip_column(const KP &p, ST *__restrict__ F, con
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const int *__restrict__ js_old,
+__global__ void __launch_bounds__(128) k_flip(const __grid_constant__ KP p, ST *__restrict__ F, const int *__restrict__ js_old,
                                               const int *__restrict__ js_new, int *__restrict__ nb_new,
                                               int inflight, int do_flip) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(128) k_flip(KP p, ST *__restrict__ F, const in
 // ----------------------------------------------------- outputs and inputs
 // T and u per node (solid: Tm and 0), natural values.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_macro(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_macro(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                const int *__restrict__ js, const float *__restrict__ thw,
                                                int inflight, float *__restrict__ T, float *__restrict__ u) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(128) k_macro(KP p, const ST *__restrict__ F, c
 // Solid nodes report f = 0; deep solid nodes (see deep_solid) report g at
 // rest at Tm, the value their slots would hold if they were updated.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_state_out(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_state_out(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                    const int *__restrict__ js, const int *__restrict__ nb,
                                                    const float *__restrict__ thw, int inflight,
                                                    float *__restrict__ fo, float *__restrict__ go) {
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(128) k_state_out(KP p, const ST *__restrict__ 
 // every step), so solid nodes are stored at rest: fh = 0 and gh = 0
 // (g at rest at Tm).
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_state_in(KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_state_in(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                                   const int *__restrict__ js, const float *__restrict__ fi,
                                                   const float *__restrict__ gi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(128) k_state_in(KP p, ST *__restrict__ F, ST *
 // Initial state: fh = 0 everywhere (rest, rho = 1); gh = w (T(a) - Tm) with
 // the given profile below the front, 0 above.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_init(KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128) k_init(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const float *__restrict__ Tprof) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(128) k_init(KP p, ST *__restrict__ F, ST *__re
 // Block partials of the liquid-node totals: sum (T - Tm), sum (rho - 1),
 // count, max |u|^2.  Fixed block and thread order: deterministic.
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(256) k_totals_part(KP p, const ST *__restrict__ F, const ST *__restrict__ G,
+__global__ void __launch_bounds__(256) k_totals_part(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                      const int *__restrict__ js, const float *__restrict__ thw,
                                                      int inflight, double *__restrict__ part) {
     __shared__ double sh[4][256];

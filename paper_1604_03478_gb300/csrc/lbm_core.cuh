@@ -93,6 +93,10 @@ __host__ __device__ constexpr int nnorm(int k) {
 }
 
 // --------------------------------------------------------- kernel params
+// Kernels take KP as a const __grid_constant__ parameter, so its fields are
+// read in place from the parameter bank; passed as a plain by-value struct
+// of this size the compiler may keep a copy in registers (the even step then
+// needed 112 instead of 70 registers a thread).
 struct KP {
     int nx, ny, nz;   // cavity
     int H;            // length along the heating axis

@@ -225,6 +225,8 @@ __global__ void k_fill_d(double *p, long long n, double v) {
 
 }  // namespace
 
+lbm_status lbm_check_status(lbm_melt *h) { return check_status(h); }
+
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
 
 LBM_API lbm_status lbm_melt_derive(const lbm_melt_grid *grid, double Ra, double Pr, double Ste, double Th,
