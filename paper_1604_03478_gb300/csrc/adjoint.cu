@@ -11,13 +11,15 @@
 // step t, from the adjoint at t+1 to the adjoint at t:
 //   k_adj_front  Eq. 6 backwards: lambda_s(t+1) -> lambda_s(t), the T of
 //                the two stencil nodes at t+1, the wall field, d/d coef;
-//   k_adj_slopes the in-plane slope terms of Eq. 6 into the neighbours;
 //   k_adj_node   streaming transposed (a push becomes a gather under the
 //                flags of t) and the collision Jacobian transposed, FP32,
 //                with d/d s_nu, s_alpha, g*beta in FP64 block partials;
-//   k_adj_ghost  the ghost populations of the state at t backwards.
-// The forward is recorded with sqrt(N)-style checkpoints; each segment is
-// recomputed forward with a natural-layout snapshot per step, then reversed.
+//   k_adj_ghost  the ghost populations of the state at t backwards, and the
+//                in-plane slope terms of Eq. 6 gathered from the neighbours.
+// k_adj_ghost_front runs the ghost adjoint of t and the front adjoint of
+// the step before in one launch.  The forward is recorded with
+// sqrt(N)-style checkpoints; each segment is recomputed forward with a
+// natural-layout snapshot per step, then reversed.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -187,69 +189,6 @@ __device__ __forceinline__ double snap_T(const KP &p, const float *snap, int col
     return p.Tm_d + t;
 }
 
-// ------------------------------------------------- reverse of Eq. 6
-// Per column: lambda_s(t) own part, slope partials wp/wq, the stencil
-// nodes' temperature adjoint added to lam1 (adjoint of the state at t+1),
-// the wall field, and d/d coef.
-template <int FACE>
-__global__ void __launch_bounds__(128) k_adj_front(const __grid_constant__ KP p, const float *__restrict__ snap1, const double *__restrict__ s,
-                                                   const float *__restrict__ thw, const double *__restrict__ lams1,
-                                                   double *__restrict__ lams0, double *__restrict__ wp,
-                                                   double *__restrict__ wq, float *__restrict__ lam1,
-                                                   double *__restrict__ lthw, double *__restrict__ lcoef) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= p.ncols) return;
-    const int P1 = p.P1, P2 = p.P2, H = p.H;
-    const int pp = col % P1, q = col / P1;
-    const double sc = s[col], Tm = p.Tm_d, Tw = (double)thw[col];
-    const double sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
-    const double sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
-    const int k = guarded_node(sc, H);
-    double G, dGds, dGdy0 = 0.0, dGdy1 = 0.0, dGdTw = 0.0;
-    long long c1 = 0, c0 = 0;
-    if (k < 0) {
-        G = (Tm - Tw) / sc;
-        dGds = -(Tm - Tw) / (sc * sc);
-        dGdTw = -1.0 / sc;
-    } else {
-        const double y1 = snap_T<FACE>(p, snap1, col, k, c1), x1 = k + 0.5;
-        const double x0 = k >= 1 ? k - 0.5 : 0.0;
-        const double y0 = k >= 1 ? snap_T<FACE>(p, snap1, col, k - 1, c0) : Tw;
-        const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
-        G = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
-        dGdy0 = d1 / (h * d0);
-        dGdy1 = -d0 / (h * d1);
-        dGds = (y0 - Tm) / (d0 * d0) + (y1 - Tm) / (d1 * d1);
-    }
-    const double fac = 1.0 + sp * sp + sq * sq;
-    const double v = p.coef * fac * (-G);
-    const double sn = sc + v;
-    const double L = lams1[col];
-    if (!(sn >= 0.5) || sn > (double)H) {  // clamped: s(t+1) does not depend on anything
-        lams0[col] = 0.0;
-        wp[col] = 0.0;
-        wq[col] = 0.0;
-        return;
-    }
-    const double a = L * p.coef * fac;  // lambda times d v / d(-G)
-    lams0[col] = L - a * dGds;
-    wp[col] = L * p.coef * (-G) * 2.0 * sp;
-    wq[col] = L * p.coef * (-G) * 2.0 * sq;
-    lcoef[col] += L * fac * (-G);
-    if (k >= 0) {
-        const float lT1 = (float)(-a * dGdy1);
-        for (int i = 0; i < 7; ++i) lam1[(19 + i) * p.N + c1] += lT1;
-        if (k >= 1) {
-            const float lT0 = (float)(-a * dGdy0);
-            for (int i = 0; i < 7; ++i) lam1[(19 + i) * p.N + c0] += lT0;
-        } else {
-            lthw[col] += -a * dGdy0;
-        }
-    } else {
-        lthw[col] += -a * dGdTw;
-    }
-}
-
 // The slopes s_p, s_q of column c' read the fronts of its neighbours (with a
 // mirror at the side walls); the sum of their d/d s for column col.
 __device__ __forceinline__ double slope_terms(const KP &p, const double *__restrict__ wp,
@@ -292,11 +231,13 @@ __global__ void __launch_bounds__(128) k_adj_node(const __grid_constant__ KP p, 
     const int z = blockIdx.z;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     float dsnu = 0.0f, dsal = 0.0f, dgb = 0.0f;
+    int liquid = 0;
     if (x < p.nx && y < p.ny) {
         const long long c = node_index(p, x, y, z);
         const long long N = p.N;
         const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
         const int jsc = js[col];
+        liquid = a < jsc;
         // heated-wall link: the node next to the wall receives
         // -g*_opp + 2 w (Tw - Tm) along the heating axis
         if (a == 0) {
@@ -349,6 +290,8 @@ __global__ void __launch_bounds__(128) k_adj_node(const __grid_constant__ KP p, 
             }
         }
     }
+    // blocks without a liquid node add nothing to the rate partials
+    if (!__syncthreads_or(liquid)) return;
     sh[0][tid] = dsnu;
     sh[1][tid] = dsal;
     sh[2][tid] = dgb;
@@ -367,85 +310,287 @@ __global__ void __launch_bounds__(128) k_adj_node(const __grid_constant__ KP p, 
     }
 }
 
-// ---------------------------------------------- ghost populations, reversed
-// g*_ghost = w (T_ghost - Tm) + N^T D^-1 (I - Q)(n_L - n^eq_L), with T_ghost
-// on the line through (s, Tm) and the guarded node (or the wall).
-// Also gathers the slope terms of Eq. 6 into lambda_s (k_adj_slopes).
+// ------------------------------------- column adjoints (Eq. 6, ghost node)
+// Two per-column pieces of a reverse step, run in one thread:
+//
+// ghost (level t): g*_ghost = w (T_ghost - Tm) + N^T D^-1 (I - Q)(n_L -
+// n^eq_L), with T_ghost on the line through (s, Tm) and the guarded node (or
+// the wall), taken backwards; also the in-plane slope terms of Eq. 6 that
+// the neighbour columns computed, gathered into lambda_s(t).
+//
+// front (step t-1 -> t): Eq. 6 backwards, lambda_s(t) -> lambda_s(t-1), the
+// temperature adjoint of the two stencil nodes at t, the slope partials
+// wp/wq (d/d s of the neighbours' slopes), the wall field and d/d coef.
+//
+// All loads that depend only on the column, the fronts and the liquid count
+// are issued before the first store; the population adjoint of every node
+// touched (ghost source, guarded node, two stencil nodes; some may coincide)
+// is read once, the contributions for that node summed, and stored.
+struct ColIn {
+    // ghost
+    int jn, kg;
+    double sn, slope, lTG;
+    float lgp[7];
+    long long ck, cL;
+    double Tk;
+    float fL[19], gL[7];
+    // front
+    int k;
+    double sc, sp, sq, y0, y1;
+    long long c1, c0;
+};
+
+template <int FACE, bool GHOST, bool FRONT>
+__device__ __forceinline__ void adj_column(const KP &p, int col, const float *__restrict__ snap,
+                                           const int *__restrict__ js, const double *__restrict__ s,
+                                           const double *__restrict__ s_prev, const float *__restrict__ thw,
+                                           const float *__restrict__ lgpost, float *__restrict__ lam,
+                                           double *__restrict__ lams, double *__restrict__ lams_prev,
+                                           double *__restrict__ lthw, double *__restrict__ lsal,
+                                           double *__restrict__ lgb, double *__restrict__ lcoef,
+                                           const double *__restrict__ wp, const double *__restrict__ wq,
+                                           double *__restrict__ wp_prev, double *__restrict__ wq_prev) {
+    const int H = p.H, P1 = p.P1, P2 = p.P2;
+    const long long N = p.N;
+    const double Tm = p.Tm_d, Tw = (double)thw[col];
+    const int pp = col % P1, q = col / P1;
+    ColIn in;
+    in.jn = H;
+    in.kg = -1;
+    in.ck = in.cL = -1;
+    in.k = -1;
+    in.c1 = in.c0 = -1;
+    // ---- loads
+    const double lams_in = lams[col];
+    if (GHOST) {
+        in.slope = slope_terms(p, wp, wq, col);
+        in.jn = js[col];
+        in.sn = s[col];
+        in.lTG = 0.0;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            in.lgp[i] = lgpost[(long long)i * p.ncols + col];
+            in.lTG += (double)w7(i) * in.lgp[i];
+        }
+        if (in.jn < H) {
+            in.kg = guarded_node(in.sn, H);
+            if (in.kg >= 0) in.Tk = snap_T<FACE>(p, snap, col, in.kg, in.ck);
+            if (in.jn >= 1) {
+                int x, y, z;
+                column_node<FACE>(p, col, in.jn - 1, x, y, z);
+                in.cL = node_index(p, x, y, z);
+#pragma unroll
+                for (int i = 0; i < 7; ++i) in.gL[i] = snap[(19 + i) * N + in.cL];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) in.fL[i] = snap[i * N + in.cL];
+            }
+        }
+    }
+    if (FRONT) {
+        in.sc = s_prev[col];
+        in.sp = 0.5 * (s_prev[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s_prev[q * P1 + (pp > 0 ? pp - 1 : pp)]);
+        in.sq = 0.5 * (s_prev[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s_prev[(q > 0 ? q - 1 : q) * P1 + pp]);
+        in.k = guarded_node(in.sc, H);
+        in.y0 = Tw;
+        if (in.k >= 0) {
+            in.y1 = snap_T<FACE>(p, snap, col, in.k, in.c1);
+            if (in.k >= 1) in.y0 = snap_T<FACE>(p, snap, col, in.k - 1, in.c0);
+        }
+    }
+    // the g adjoint of up to four nodes: ghost source, guarded node, stencil
+    long long nd[4] = {in.cL, in.ck, in.c1, in.c0};
+    float base[4][7];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (nd[e] >= 0) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) base[e][i] = lam[(19 + i) * N + nd[e]];
+        }
+    float add[4][7];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int i = 0; i < 7; ++i) add[e][i] = 0.0f;
+    float fadd[19];
+    double dthw = 0.0;
+    double Ls = lams_in;  // lambda_s of level t, completed below
+    // ---- ghost, backwards
+    if (GHOST) {
+        Ls += in.slope;
+        if (in.jn < H) {
+            const double sn = in.sn, yg = in.jn + 0.5, lTG = in.lTG;
+            if (in.kg < 0) {
+                dthw += -(yg - sn) / sn * lTG;
+                Ls += (Tm - Tw) * (-yg / (sn * sn)) * lTG;
+            } else {
+                const double yk = in.kg + 0.5, r = (yg - sn) / (sn - yk);
+                const float lTk = (float)(-r * lTG);
+#pragma unroll
+                for (int i = 0; i < 7; ++i) add[1][i] = lTk;
+                Ls += (Tm - in.Tk) * (-(yg - yk) / ((sn - yk) * (sn - yk))) * lTG;
+            }
+            if (in.jn >= 1) {
+                const float *gL = in.gL, *fL = in.fL, *lgp = in.lgp;
+                float Th = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) Th += gL[i];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) { jx += ex(i) * fL[i]; jy += ey(i) * fL[i]; jz += ez(i) * fL[i]; }
+                const float TL = Th + p.Tm;
+                const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
+                constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+                constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+                const float Nl1 = lgp[1] - lgp[2], Nl2 = lgp[3] - lgp[4], Nl3 = lgp[5] - lgp[6];
+                const float Nl4 = 6.0f * lgp[0] - (lgp[1] + lgp[2] + lgp[3] + lgp[4] + lgp[5] + lgp[6]);
+                const float Nl5 = 2.0f * (lgp[1] + lgp[2]) - (lgp[3] + lgp[4] + lgp[5] + lgp[6]);
+                const float Nl6 = (lgp[3] + lgp[4]) - (lgp[5] + lgp[6]);
+                const float d1 = (gL[1] - gL[2]) - ux * TL, d2 = (gL[3] - gL[4]) - uy * TL,
+                            d3 = (gL[5] - gL[6]) - uz * TL;
+                lsal[col] += -(double)(i1 * (Nl1 * d1 + Nl2 * d2 + Nl3 * d3));
+                const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
+                float mu[7];
+                mu[0] = 0.0f;
+                mu[1] = ra * i1 * Nl1;
+                mu[2] = ra * i1 * Nl2;
+                mu[3] = ra * i1 * Nl3;
+                mu[4] = r4 * i4 * Nl4;
+                mu[5] = r5 * i5 * Nl5;
+                mu[6] = r5 * i6 * Nl6;
+                const float lux = -mu[1] * TL, luy = -mu[2] * TL, luz = -mu[3] * TL;
+                const float lTh = -(mu[1] * ux + mu[2] * uy + mu[3] * uz) - 0.75f * mu[4] + 0.5f * p.gbeta * luz;
+                lgb[col] += 0.5 * (double)Th * (double)luz;
+                float og[7];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) og[i] = lTh;
+                add_back7_all<0>(og, mu);
+#pragma unroll
+                for (int i = 0; i < 7; ++i) add[0][i] = og[i];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) fadd[i] = ex(i) * lux + ey(i) * luy + ez(i) * luz;
+            }
+        }
+        lams[col] = Ls;
+    }
+    // ---- front of the step before, backwards (lambda_s of level t = Ls)
+    if (FRONT) {
+        const double sc = in.sc, sp = in.sp, sq = in.sq;
+        const int k = in.k;
+        double G, dGds, dGdy0 = 0.0, dGdy1 = 0.0, dGdTw = 0.0;
+        if (k < 0) {
+            G = (Tm - Tw) / sc;
+            dGds = -(Tm - Tw) / (sc * sc);
+            dGdTw = -1.0 / sc;
+        } else {
+            const double y1 = in.y1, y0 = in.y0, x1 = k + 0.5;
+            const double x0 = k >= 1 ? k - 0.5 : 0.0;
+            const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
+            G = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
+            dGdy0 = d1 / (h * d0);
+            dGdy1 = -d0 / (h * d1);
+            dGds = (y0 - Tm) / (d0 * d0) + (y1 - Tm) / (d1 * d1);
+        }
+        const double fac = 1.0 + sp * sp + sq * sq;
+        const double v = p.coef * fac * (-G);
+        const double sn = sc + v;
+        if (!(sn >= 0.5) || sn > (double)H) {  // clamped: s(t) does not depend on anything
+            lams_prev[col] = 0.0;
+            wp_prev[col] = 0.0;
+            wq_prev[col] = 0.0;
+            nd[2] = nd[3] = -1;
+        } else {
+            const double a = Ls * p.coef * fac;  // lambda times d v / d(-G)
+            lams_prev[col] = Ls - a * dGds;
+            wp_prev[col] = Ls * p.coef * (-G) * 2.0 * sp;
+            wq_prev[col] = Ls * p.coef * (-G) * 2.0 * sq;
+            lcoef[col] += Ls * fac * (-G);
+            if (k >= 0) {
+                const float lT1 = (float)(-a * dGdy1);
+#pragma unroll
+                for (int i = 0; i < 7; ++i) add[2][i] = lT1;
+                if (k >= 1) {
+                    const float lT0 = (float)(-a * dGdy0);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) add[3][i] = lT0;
+                } else {
+                    dthw += -a * dGdy0;
+                }
+            } else {
+                dthw += -a * dGdTw;
+            }
+        }
+    }
+    // ---- stores: each touched node gets its base plus every contribution
+    // aimed at it (coinciding entries store the same value)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (nd[e] < 0) continue;
+        float v[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) v[i] = base[e][i];
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+            if (nd[o] == nd[e]) {
+#pragma unroll
+                for (int i = 0; i < 7; ++i) v[i] += add[o][i];
+            }
+#pragma unroll
+        for (int i = 0; i < 7; ++i) lam[(19 + i) * N + nd[e]] = v[i];
+    }
+    if (GHOST && in.cL >= 0) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) lam[i * N + in.cL] += fadd[i];
+    }
+    if (dthw != 0.0) lthw[col] += dthw;
+}
+
+// Front adjoint of the step t -> t+1 alone (top of a segment): snap and lam
+// of level t+1, lambda_s(t+1) in lams1, lambda_s(t) and the slope partials
+// of level t out.
 template <int FACE>
-__global__ void __launch_bounds__(128) k_adj_ghost(const __grid_constant__ KP p, const float *__restrict__ snap, const int *__restrict__ js,
+__global__ void __launch_bounds__(128) k_adj_front(const __grid_constant__ KP p, const float *__restrict__ snap1,
                                                    const double *__restrict__ s, const float *__restrict__ thw,
-                                                   const float *__restrict__ lgpost, float *__restrict__ lam0,
-                                                   double *__restrict__ lams0, double *__restrict__ lthw,
-                                                   double *__restrict__ lsal, double *__restrict__ lgb,
-                                                   const double *__restrict__ wp, const double *__restrict__ wq) {
+                                                   double *__restrict__ lams1, double *__restrict__ lams0,
+                                                   double *__restrict__ wp, double *__restrict__ wq,
+                                                   float *__restrict__ lam1, double *__restrict__ lthw,
+                                                   double *__restrict__ lcoef) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= p.ncols) return;
-    lams0[col] += slope_terms(p, wp, wq, col);
-    const int H = p.H, jn = js[col];
-    if (jn >= H) return;
-    const long long N = p.N;
-    const double sn = s[col], Tm = p.Tm_d, Tw = (double)thw[col];
-    const double yg = jn + 0.5;
-    float lgp[7];
-    double lTG = 0.0;
-    for (int i = 0; i < 7; ++i) {
-        lgp[i] = lgpost[(long long)i * p.ncols + col];
-        lTG += (double)w7(i) * lgp[i];
-    }
-    const int kg = guarded_node(sn, H);
-    if (kg < 0) {
-        lthw[col] += -(yg - sn) / sn * lTG;
-        lams0[col] += (Tm - Tw) * (-yg / (sn * sn)) * lTG;
-    } else {
-        int x, y, z;
-        column_node<FACE>(p, col, kg, x, y, z);
-        const long long ck = node_index(p, x, y, z);
-        double Tk = Tm;
-        for (int i = 0; i < 7; ++i) Tk += (double)snap[(19 + i) * N + ck];
-        const double yk = kg + 0.5, r = (yg - sn) / (sn - yk);
-        const float lTk = (float)(-r * lTG);
-        for (int i = 0; i < 7; ++i) lam0[(19 + i) * N + ck] += lTk;
-        lams0[col] += (Tm - Tk) * (-(yg - yk) / ((sn - yk) * (sn - yk))) * lTG;
-    }
-    if (jn < 1) return;
-    int x, y, z;
-    column_node<FACE>(p, col, jn - 1, x, y, z);
-    const long long cL = node_index(p, x, y, z);
-    float gL[7], fL[19];
-    for (int i = 0; i < 7; ++i) gL[i] = snap[(19 + i) * N + cL];
-    for (int i = 0; i < 19; ++i) fL[i] = snap[i * N + cL];
-    float Th = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    for (int i = 0; i < 7; ++i) Th += gL[i];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) { jx += ex(i) * fL[i]; jy += ey(i) * fL[i]; jz += ez(i) * fL[i]; }
-    const float TL = Th + p.Tm;
-    const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
-    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
-    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
-    const float Nl1 = lgp[1] - lgp[2], Nl2 = lgp[3] - lgp[4], Nl3 = lgp[5] - lgp[6];
-    const float Nl4 = 6.0f * lgp[0] - (lgp[1] + lgp[2] + lgp[3] + lgp[4] + lgp[5] + lgp[6]);
-    const float Nl5 = 2.0f * (lgp[1] + lgp[2]) - (lgp[3] + lgp[4] + lgp[5] + lgp[6]);
-    const float Nl6 = (lgp[3] + lgp[4]) - (lgp[5] + lgp[6]);
-    const float d1 = (gL[1] - gL[2]) - ux * TL, d2 = (gL[3] - gL[4]) - uy * TL, d3 = (gL[5] - gL[6]) - uz * TL;
-    lsal[col] += -(double)(i1 * (Nl1 * d1 + Nl2 * d2 + Nl3 * d3));
-    const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
-    float mu[7];
-    mu[0] = 0.0f;
-    mu[1] = ra * i1 * Nl1;
-    mu[2] = ra * i1 * Nl2;
-    mu[3] = ra * i1 * Nl3;
-    mu[4] = r4 * i4 * Nl4;
-    mu[5] = r5 * i5 * Nl5;
-    mu[6] = r5 * i6 * Nl6;
-    const float lux = -mu[1] * TL, luy = -mu[2] * TL, luz = -mu[3] * TL;
-    const float lTh = -(mu[1] * ux + mu[2] * uy + mu[3] * uz) - 0.75f * mu[4] + 0.5f * p.gbeta * luz;
-    lgb[col] += 0.5 * (double)Th * (double)luz;
-    float og[7];
-    for (int i = 0; i < 7; ++i) og[i] = lTh;
-    add_back7_all<0>(og, mu);
-    for (int i = 0; i < 7; ++i) lam0[(19 + i) * N + cL] += og[i];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) lam0[i * N + cL] += ex(i) * lux + ey(i) * luy + ez(i) * luz;
+    adj_column<FACE, false, true>(p, col, snap1, nullptr, nullptr, s, thw, nullptr, lam1, lams1, lams0, lthw, nullptr,
+                                  nullptr, lcoef, nullptr, nullptr, wp, wq);
+}
+
+// Ghost adjoint of level t alone (t = 0 of a segment).
+template <int FACE>
+__global__ void __launch_bounds__(128) k_adj_ghost(const __grid_constant__ KP p, const float *__restrict__ snap,
+                                                   const int *__restrict__ js, const double *__restrict__ s,
+                                                   const float *__restrict__ thw, const float *__restrict__ lgpost,
+                                                   float *__restrict__ lam0, double *__restrict__ lams0,
+                                                   double *__restrict__ lthw, double *__restrict__ lsal,
+                                                   double *__restrict__ lgb, const double *__restrict__ wp,
+                                                   const double *__restrict__ wq) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    adj_column<FACE, true, false>(p, col, snap, js, s, nullptr, thw, lgpost, lam0, lams0, nullptr, lthw, lsal, lgb,
+                                  nullptr, wp, wq, nullptr, nullptr);
+}
+
+// The ghost adjoint of level t, then the front adjoint of the step t-1 -> t
+// for the same column: the latter needs lambda_s of level t only in its own
+// column, adds to the level-t population adjoint only in its own column and
+// writes its slope partials to the other of two buffers (the neighbours'
+// ghost adjoints still read the level-t ones), so one launch does both.
+template <int FACE>
+__global__ void __launch_bounds__(128) k_adj_ghost_front(
+    const __grid_constant__ KP p, const float *__restrict__ snap, const int *__restrict__ js,
+    const double *__restrict__ s, const double *__restrict__ s_prev, const float *__restrict__ thw,
+    const float *__restrict__ lgpost, float *__restrict__ lam0, double *__restrict__ lams0,
+    double *__restrict__ lams_prev, double *__restrict__ lthw, double *__restrict__ lsal, double *__restrict__ lgb,
+    double *__restrict__ lcoef, const double *__restrict__ wp, const double *__restrict__ wq,
+    double *__restrict__ wp_prev, double *__restrict__ wq_prev) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    adj_column<FACE, true, true>(p, col, snap, js, s, s_prev, thw, lgpost, lam0, lams0, lams_prev, lthw, lsal, lgb,
+                                 lcoef, wp, wq, wp_prev, wq_prev);
 }
 
 // Deterministic FP64 sum of n values (one block), times scale, added to *out.
@@ -590,11 +735,13 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     const long long C = t->C;
     const dim3 blk = lbm::node_block(p), grd = lbm::node_grid(p, blk);
     const size_t nblk = (size_t)grd.x * grd.y * grd.z;
-    const int cgrid = (int)((nc + 127) / 128);
+    const int cb = h->cblk;
+    const dim3 cgrid = lbm::col_grid((long long)nc, cb);
     // buffers
     unsigned char *fin = nullptr;
     float *snap = nullptr, *lam[2] = {nullptr, nullptr}, *lgpost = nullptr;
-    double *snap_s = nullptr, *lams[2] = {nullptr, nullptr}, *wp = nullptr, *wq = nullptr, *lthw = nullptr;
+    double *snap_s = nullptr, *lams[2] = {nullptr, nullptr}, *wp[2] = {nullptr, nullptr}, *wq[2] = {nullptr, nullptr};
+    double *lthw = nullptr;
     double *part = nullptr, *lsal = nullptr, *lgb = nullptr, *lcoef = nullptr, *acc = nullptr;
     int *snap_js = nullptr, *snap_nb = nullptr;
     struct Alloc { void **p; size_t b; } al[] = {
@@ -602,7 +749,8 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         {(void **)&snap_s, (size_t)(C + 1) * nc * 8}, {(void **)&snap_js, (size_t)(C + 1) * nc * 4},
         {(void **)&snap_nb, (size_t)(C + 1) * nc * 4},
         {(void **)&lam[0], 26 * N * 4}, {(void **)&lam[1], 26 * N * 4}, {(void **)&lgpost, 7 * nc * 4},
-        {(void **)&lams[0], nc * 8}, {(void **)&lams[1], nc * 8}, {(void **)&wp, nc * 8}, {(void **)&wq, nc * 8},
+        {(void **)&lams[0], nc * 8}, {(void **)&lams[1], nc * 8}, {(void **)&wp[0], nc * 8}, {(void **)&wq[0], nc * 8},
+        {(void **)&wp[1], nc * 8}, {(void **)&wq[1], nc * 8},
         {(void **)&lthw, nc * 8}, {(void **)&part, nblk * 3 * 8}, {(void **)&lsal, nc * 8},
         {(void **)&lgb, nc * 8}, {(void **)&lcoef, nc * 8}, {(void **)&acc, 4 * 8}};
     lbm_status st = LBM_OK;
@@ -666,14 +814,28 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             const double *st_s = snap_s + (size_t)j * nc;
             const int *st_js = snap_js + (size_t)j * nc;
             const int *st_nb = snap_nb + (size_t)j * nc;
+            // Level j: the front adjoint of step j -> j+1 (run by the
+            // previous iteration's fused launch, except at the top of the
+            // segment), the node adjoint, then the ghost adjoint fused with
+            // the front adjoint of step j-1 -> j (alone at j = 0).
+            const int pj = (int)(j & 1), pm = pj ^ 1;
+            const double *st_s_prev = j > 0 ? snap_s + (size_t)(j - 1) * nc : nullptr;
             if (h->face == 0) {
-                lbm::k_adj_front<0><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
+                if (j == len - 1)
+                    lbm::k_adj_front<0><<<cgrid, cb, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp[pj], wq[pj], lam[1], lthw, lcoef);
                 lbm::k_adj_node<0><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
-                lbm::k_adj_ghost<0><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp, wq);
+                if (j > 0)
+                    lbm::k_adj_ghost_front<0><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lam[0], lams[0], lams[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
+                else
+                    lbm::k_adj_ghost<0><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp[pj], wq[pj]);
             } else {
-                lbm::k_adj_front<1><<<cgrid, 128, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp, wq, lam[1], lthw, lcoef);
+                if (j == len - 1)
+                    lbm::k_adj_front<1><<<cgrid, cb, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp[pj], wq[pj], lam[1], lthw, lcoef);
                 lbm::k_adj_node<1><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
-                lbm::k_adj_ghost<1><<<cgrid, 128, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp, wq);
+                if (j > 0)
+                    lbm::k_adj_ghost_front<1><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lam[0], lams[0], lams[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
+                else
+                    lbm::k_adj_ghost<1><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp[pj], wq[pj]);
             }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { st = tape_err(h, LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e)); break; }

@@ -45,6 +45,7 @@ struct lbm_melt {
     size_t bytes;
     int timing;
     int bx, by;        // block shape of the per-node kernels (0: default)
+    int cblk;          // threads per block of the per-column kernels
     double Ra;         // as given to create
     int derived_from_Ra;
     void *tape;        // recorded run for the adjoint (adjoint.cu)

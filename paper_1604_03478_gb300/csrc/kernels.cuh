@@ -262,16 +262,52 @@ __device__ __forceinline__ void gather_f(const KP &p, const ST *F, const int *js
     }
 }
 
+// Liquid counts of the 3x3 columns around column (pp, q), 0 outside the
+// cavity; entry (dq + 1) * 3 + dp + 1.
+__device__ __forceinline__ void load_js9(const KP &p, const int *__restrict__ js, int pp, int q, int (&js9)[9]) {
+#pragma unroll
+    for (int dq = -1; dq <= 1; ++dq)
+#pragma unroll
+        for (int dp = -1; dp <= 1; ++dp) {
+            const int p2 = pp + dp, q2 = q + dq;
+            const bool in = (unsigned)p2 < (unsigned)p.P1 && (unsigned)q2 < (unsigned)p.P2;
+            js9[(dq + 1) * 3 + dp + 1] = in ? __ldg(js + q2 * p.P1 + p2) : 0;
+        }
+}
+
+// gather_f in flight for the node at height a of the middle column, with
+// the liquid tests read from js9 (load_js9) instead of memory.
+template <typename ST, int FACE>
+__device__ __forceinline__ void gather_f9(const KP &p, const ST *F, const int (&js9)[9], int x, int y, int z, int a,
+                                          float (&f)[19]) {
+    const long long c = node_index(p, x, y, z);
+    f[0] = Store<ST>::ld(F + c);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        // the upstream node x - e_i: in-plane column offset and height
+        const int dp = -ex(i), dq = FACE == 0 ? -ez(i) : -ey(i), da = FACE == 0 ? -ey(i) : -ez(i);
+        const int an = a + da;
+        const bool liq = an >= 0 && an < js9[(dq + 1) * 3 + dp + 1];
+        if (liq) f[i] = Store<ST>::ld(F + opp(i) * p.ld + (c - off19<FACE>(p, i)));
+        else f[i] = Store<ST>::ld(F + i * p.ld + c);
+    }
+}
+
+// Tm + the sum of the shifted g, in FP64 (the temperature the front reads).
+__device__ __forceinline__ double sum_T(const KP &p, const float (&g)[7]) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) t += (double)g[i];
+    return p.Tm_d + t;
+}
+
 template <typename ST, int FACE>
 __device__ __forceinline__ double node_T(const KP &p, const ST *G, int col, int j, bool inflight, const float *thw) {
     int x, y, z;
     column_node<FACE>(p, col, j, x, y, z);
     float g[7];
     gather_g<ST, FACE>(p, G, x, y, z, inflight, thw, g);
-    double t = 0.0;
-#pragma unroll
-    for (int i = 0; i < 7; ++i) t += (double)g[i];
-    return p.Tm_d + t;
+    return sum_T(p, g);
 }
 
 // Highest node at least half a cell below s (centre j + 1/2 <= s - 1/2).
@@ -296,15 +332,41 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
                                            int move, int *__restrict__ status, int col) {
     const int P1 = p.P1, P2 = p.P2, H = p.H;
     const int pp = col % P1, q = col / P1;
+    const bool infl = inflight != 0;
+    // Round 1: what depends on the column only.
     const double sc = s[col];
     const double Tm = p.Tm_d;
     const double Tw = (double)thw[col];
-    const bool infl = inflight != 0;
+    const int jsc = js[col];
+    int js9[9];
+    if (infl) load_js9(p, js, pp, q, js9);
+    double sp = 0.0, sq = 0.0;
+    if (move) {
+        sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
+        sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
+    }
+    // Round 2: the gradient stencil of s_t and, speculatively, the node
+    // below the current front, which is the ghost's source node whenever the
+    // liquid count does not change (all but a few columns per step).
+    const int k = move ? guarded_node(sc, H) : -2;
+    double y1 = 0.0, y0 = Tw;
+    if (k >= 0) {
+        y1 = node_T<ST, FACE>(p, G, col, k, infl, thw);
+        if (k >= 1) y0 = node_T<ST, FACE>(p, G, col, k - 1, infl, thw);
+    }
+    const int L = jsc - 1;
+    const bool spec = L >= 0 && jsc < H;
+    float gL[7], fL[19];
+    if (spec) {
+        int x, y, z;
+        column_node<FACE>(p, col, L, x, y, z);
+        gather_g<ST, FACE>(p, G, x, y, z, infl, thw, gL);
+        if (infl) gather_f9<ST, FACE>(p, F, js9, x, y, z, L, fL);
+        else gather_f<ST, FACE>(p, F, js, x, y, z, false, fL);
+    }
+    // Round 3: Eq. 6.
     double sn = sc;
     if (move) {
-        const double sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
-        const double sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
-        const int k = guarded_node(sc, H);
         double Gr;
         if (k < 0) {
             Gr = (Tm - Tw) / sc;
@@ -312,10 +374,8 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
             // derivative at x2 = s of the quadratic through (x0, y0), (x1, y1),
             // (x2, Tm): with h = x1 - x0, d1 = x2 - x1, d0 = x2 - x0,
             // p'(x2) = (y0 d1^2 - y1 d0^2 + Tm h (d0 + d1)) / (h d0 d1)
-            const double y1 = node_T<ST, FACE>(p, G, col, k, infl, thw);
             const double x1 = k + 0.5;
             const double x0 = k >= 1 ? k - 0.5 : 0.0;
-            const double y0 = k >= 1 ? node_T<ST, FACE>(p, G, col, k - 1, infl, thw) : Tw;
             const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
             Gr = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
         }
@@ -334,8 +394,16 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
     const double yg = jn + 0.5;
     const int kg = guarded_node(sn, H);
     double Tg;
-    if (kg < 0) Tg = Tm + (Tm - Tw) * (yg - sn) / sn;
-    else Tg = Tm + (Tm - node_T<ST, FACE>(p, G, col, kg, infl, thw)) * (yg - sn) / (sn - (kg + 0.5));
+    if (kg < 0) {
+        Tg = Tm + (Tm - Tw) * (yg - sn) / sn;
+    } else {
+        double Tk;
+        if (kg == k) Tk = y1;
+        else if (kg == k - 1 && k >= 1) Tk = y0;
+        else if (spec && kg == L) Tk = sum_T(p, gL);
+        else Tk = node_T<ST, FACE>(p, G, col, kg, infl, thw);
+        Tg = Tm + (Tm - Tk) * (yg - sn) / (sn - (kg + 0.5));
+    }
     // ghost populations (FP32, like the collision): rest equilibrium at the
     // ghost temperature plus the non-equilibrium part N^-1 (I - Q)(n - n^eq)
     // of the post-collision populations of the liquid node below
@@ -344,16 +412,17 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
 #pragma unroll
     for (int i = 0; i < 7; ++i) gh[i] = w7(i) * dTg;
     if (jn >= 1) {
-        int x, y, z;
-        column_node<FACE>(p, col, jn - 1, x, y, z);
-        float gL[7], fL[19];
-        gather_g<ST, FACE>(p, G, x, y, z, infl, thw, gL);
-        const bool newly_liquid = (jn - 1) >= js[col];
-        if (newly_liquid) {
+        if (!(spec && jn == jsc)) {  // the count changed: the source node moved
+            int x, y, z;
+            column_node<FACE>(p, col, jn - 1, x, y, z);
+            gather_g<ST, FACE>(p, G, x, y, z, infl, thw, gL);
+            const bool newly_liquid = (jn - 1) >= jsc;
+            if (newly_liquid) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) fL[i] = 0.0f;
-        } else {
-            gather_f<ST, FACE>(p, F, js, x, y, z, infl, fL);
+                for (int i = 0; i < 19; ++i) fL[i] = 0.0f;
+            } else {
+                gather_f<ST, FACE>(p, F, js, x, y, z, infl, fL);
+            }
         }
         float Th = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll

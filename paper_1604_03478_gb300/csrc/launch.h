@@ -20,6 +20,7 @@ struct Bufs {
     const float *thw_rd, *thw_wr;
     int *status;
     const Links *lk;             // interior link offsets of the odd step
+    int cblk;                    // threads per block of the per-column kernels (col_block)
 };
 
 template <typename ST> struct Launch {
@@ -33,6 +34,17 @@ template <typename ST> struct Launch {
     static cudaError_t totals(const KP &p, int face, int inflight, const Bufs &b, double *part, int nparts,
                               double t, double *out, cudaStream_t st);
 };
+
+// Threads per block of the per-column kernels (front, flip and their
+// adjoints): the largest of 128, 64 and 32 that still gives two blocks per
+// SM, so that a small front (96 x 96 columns) spreads its FP64 arithmetic
+// over all SMs instead of half of them.
+inline int col_block(long long ncols, int sms) {
+    for (int b = 128; b > 32; b >>= 1)
+        if ((ncols + b - 1) / b >= 2LL * sms) return b;
+    return 32;
+}
+inline dim3 col_grid(long long ncols, int b) { return dim3((unsigned)((ncols + b - 1) / b)); }
 
 // Block shape for the per-node kernels: 128 threads, x-major.
 inline dim3 node_block(const KP &p) {

@@ -23,7 +23,7 @@ cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Buf
 
 template <typename ST>
 cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st) {
-    dim3 blk(128), grd((p.ncols + 127) / 128);
+    const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
         k_front<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status);
@@ -34,7 +34,7 @@ cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, con
 
 template <typename ST>
 cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, int do_flip, const Bufs &b, cudaStream_t st) {
-    dim3 blk(128), grd((p.ncols + 127) / 128);
+    const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     ST *F = (ST *)b.F;
     if (face == 0) k_flip<ST, 0><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
     else k_flip<ST, 1><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);

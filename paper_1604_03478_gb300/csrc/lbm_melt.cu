@@ -151,6 +151,7 @@ Bufs bufs(lbm_melt *h) {
     b.thw_wr = h->thw_cur;
     b.status = h->status_dev;
     b.lk = &h->lk;
+    b.cblk = h->cblk;
     return b;
 }
 
@@ -304,6 +305,12 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     }
     auto fail = [&](lbm_status s) { free_all(h); delete h; return s; };
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(LBM_ECUDA);
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1)
+            return fail(LBM_ECUDA);
+        h->cblk = lbm::col_block(h->kp.ncols, sms);
+    }
     const size_t es = h->precision == 1 ? sizeof(__half) : sizeof(float);
     const size_t nF = 19 * (size_t)p.ld * es, nG = 7 * (size_t)p.ld * es;
     const size_t nc = (size_t)d.ncols;
