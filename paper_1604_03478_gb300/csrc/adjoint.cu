@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -733,8 +734,20 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     const lbm::KP &p = h->kp;
     const size_t N = (size_t)p.N, nc = (size_t)p.ncols;
     const long long C = t->C;
-    const dim3 blk = lbm::node_block(p), grd = lbm::node_grid(p, blk);
-    const size_t nblk = (size_t)grd.x * grd.y * grd.z;
+    const dim3 blk = lbm::node_block(p);
+    const dim3 grd_all = lbm::node_grid(p, blk);
+    const size_t nblk = (size_t)grd_all.x * grd_all.y * grd_all.z;
+    // Every level of the recorded run has liquid counts at most the running
+    // maximum; the snapshot and the node adjoint touch nothing three or more
+    // nodes above it (deep solid), so their grids stop there.
+    int abound = p.H;
+    if (p.skip_deep && !h->jmax_stale) {
+        int jm = 0;
+        if (cudaMemcpy(&jm, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return tape_err(h, LBM_ECUDA, "liquid-count maximum");
+        abound = std::min(p.H, jm + 3);
+    }
+    const dim3 grd = lbm::node_grid_axial(p, blk, h->face, abound);
     const int cb = h->cblk;
     const dim3 cgrid = lbm::col_grid((long long)nc, cb);
     // buffers

@@ -348,6 +348,7 @@ void advance_handles(lbm_ensemble *e, long long n) {
         h->steps += n;
         if (n & 1) { h->cur ^= 1; h->inflight ^= 1; }
         if (n > 0) h->thw_pending = 0;
+        if (n > 0) lbm_jmax_invalidate(h);  // its fronts moved without the running maximum
     }
     e->steps += n;
 }

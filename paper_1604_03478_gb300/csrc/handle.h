@@ -46,6 +46,19 @@ struct lbm_melt {
     int timing;
     int bx, by;        // block shape of the per-node kernels (0: default)
     int cblk;          // threads per block of the per-column kernels
+    // Height bound of the stream-collide grid (solid nodes two above every
+    // liquid count of their neighbourhood do nothing): k_front keeps a
+    // running maximum of the liquid counts on the device, read back
+    // asynchronously every few steps; a count grows by at most one a step.
+    int *jmax_dev;
+    int *jmax_host;    // pinned landing slot of the read-back
+    cudaEvent_t jmax_ev;
+    int jmax_pending;  // a read-back is in flight
+    int jmax_stale;    // jmax_dev may be below the counts (advanced elsewhere)
+    long long jmax_pending_at;  // exec_steps when it was enqueued
+    int ab_known;      // last maximum read, -1: unknown
+    long long ab_at;   // exec_steps at which ab_known held
+    long long exec_steps;  // steps this handle executed (never rewound)
     double Ra;         // as given to create
     int derived_from_Ra;
     void *tape;        // recorded run for the adjoint (adjoint.cu)
@@ -60,3 +73,6 @@ void lbm_tape_free(lbm_melt *h);
 // LBM_EUNSTABLE after a step with |ds| > 1/2, LBM_ENAN after a non-finite
 // front temperature, else LBM_OK.
 lbm_status lbm_check_status(lbm_melt *h);
+// Forget the host's view of the liquid-count maximum: after the state was
+// advanced by other code (the ensemble) or replaced.
+void lbm_jmax_invalidate(lbm_melt *h);

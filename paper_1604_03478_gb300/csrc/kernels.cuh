@@ -325,7 +325,7 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // front: g*_ghost = g^eq(T_ghost, 0) + (g*_L - g^eq(T_L, u_L)).
 // move = 0 keeps the front (used to prepare the ghost after a state upload).
 template <typename ST, int FACE>
-__device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
+__device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
                                            const int *__restrict__ js, int *__restrict__ js_next,
                                            const double *__restrict__ s, double *__restrict__ s_next,
                                            float *__restrict__ gpost, const float *__restrict__ thw, int inflight,
@@ -390,7 +390,7 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
     int jn = (int)ceil(sn - 0.5);
     jn = jn < 0 ? 0 : (jn > H ? H : jn);
     js_next[col] = jn;
-    if (jn >= H) return;  // fully liquid column: no ghost node
+    if (jn >= H) return jn;  // fully liquid column: no ghost node
     const double yg = jn + 0.5;
     const int kg = guarded_node(sn, H);
     double Tg;
@@ -450,17 +450,26 @@ __device__ __forceinline__ void front_column(const KP &p, const ST *__restrict__
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) gpost[(long long)i * p.ncols + col] = gh[i];
+    return jn;
 }
 
+// jmax (may be null): running maximum of the liquid counts, one atomic per
+// warp; the host reads it back now and then to bound the height of the
+// stream-collide grid (nodes two above every neighbouring count are deep
+// solid and do nothing).
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_front(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                const int *__restrict__ js, int *__restrict__ js_next,
                                                const double *__restrict__ s, double *__restrict__ s_next,
                                                float *__restrict__ gpost, const float *__restrict__ thw,
-                                               int inflight, int move, int *__restrict__ status) {
+                                               int inflight, int move, int *__restrict__ status,
+                                               int *__restrict__ jmax) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= p.ncols) return;
-    front_column<ST, FACE>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col);
+    int jn = -1;
+    if (col < p.ncols) jn = front_column<ST, FACE>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col);
+    // blocks are whole warps and every thread of the grid reaches this point
+    const int m = __reduce_max_sync(0xffffffffu, jn);
+    if (jmax && (threadIdx.x & 31) == 0 && m >= 0) atomicMax(jmax, m);
 }
 
 

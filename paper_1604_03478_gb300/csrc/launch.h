@@ -21,6 +21,8 @@ struct Bufs {
     int *status;
     const Links *lk;             // interior link offsets of the odd step
     int cblk;                    // threads per block of the per-column kernels (col_block)
+    int *jmax;                   // running maximum of the liquid counts (k_front), or null
+    int abound;                  // stream-collide covers heights < abound only (all above are deep solid)
 };
 
 template <typename ST> struct Launch {
@@ -53,6 +55,19 @@ inline dim3 node_block(const KP &p) {
 }
 inline dim3 node_grid(const KP &p, dim3 b) {
     return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+}
+// node_grid cut to the heights a < abound along the heating axis (y for
+// face 0, z for face 1).
+inline dim3 node_grid_axial(const KP &p, dim3 b, int face, int abound) {
+    dim3 g = node_grid(p, b);
+    if (abound < 1) abound = 1;
+    if (face == 0) {
+        const unsigned gy = (unsigned)((abound + (int)b.y - 1) / (int)b.y);
+        if (gy < g.y) g.y = gy;
+    } else if ((unsigned)abound < g.z) {
+        g.z = (unsigned)abound;
+    }
+    return g;
 }
 
 }  // namespace lbm

@@ -9,7 +9,7 @@ namespace lbm {
 
 template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
-    dim3 grd = node_grid(p, blk);
+    const dim3 grd = node_grid_axial(p, blk, face, b.abound);
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
         if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk);
@@ -26,9 +26,9 @@ cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, con
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
-        k_front<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status);
+        k_front<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
     else
-        k_front<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status);
+        k_front<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
     return cudaGetLastError();
 }
 

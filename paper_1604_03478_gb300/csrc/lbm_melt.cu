@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -152,6 +153,8 @@ Bufs bufs(lbm_melt *h) {
     b.status = h->status_dev;
     b.lk = &h->lk;
     b.cblk = h->cblk;
+    b.jmax = h->jmax_dev;
+    b.abound = h->kp.H;
     return b;
 }
 
@@ -196,8 +199,53 @@ void free_all(lbm_melt *h) {
     cudaFree(h->red_part);
     cudaFree(h->totals_dev);
     cudaFree(h->report);
+    cudaFree(h->jmax_dev);
+    if (h->jmax_host) cudaFreeHost(h->jmax_host);
+    if (h->jmax_ev) cudaEventDestroy(h->jmax_ev);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
+}
+
+// Running maximum of js over n columns into *jmax (one atomic per warp).
+__global__ void k_jmax(const int *__restrict__ js, long long n, int *__restrict__ jmax) {
+    int m = -1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, js[i]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m >= 0) atomicMax(jmax, m);
+}
+
+// Height bound for the next stream-collide: all heights when deep solid
+// nodes are updated (Tc below Tm) or while the maximum is unknown.
+int axial_bound(lbm_melt *h) {
+    const int H = h->kp.H;
+    if (!h->kp.skip_deep) return H;
+    if (h->jmax_pending) {
+        const cudaError_t e = cudaEventQuery(h->jmax_ev);
+        if (e == cudaSuccess) {
+            h->ab_known = *h->jmax_host;
+            h->ab_at = h->jmax_pending_at;
+            h->jmax_pending = 0;
+        } else if (e == cudaErrorNotReady) {
+            (void)cudaGetLastError();  // not an error: the copy is still in flight
+        }
+    }
+    if (h->ab_known < 0) return H;
+    const long long b = (long long)h->ab_known + (h->exec_steps - h->ab_at) + 3;
+    return b < H ? (int)b : H;
+}
+
+// After a step: enqueue a read-back of the running maximum every 16 steps.
+cudaError_t jmax_readback(lbm_melt *h) {
+    if (!h->kp.skip_deep || h->jmax_pending) return cudaSuccess;
+    if (h->ab_known >= 0 && h->exec_steps - h->ab_at < 16) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(h->jmax_host, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->jmax_ev, h->stream);
+    if (e == cudaSuccess) {
+        h->jmax_pending = 1;
+        h->jmax_pending_at = h->exec_steps;
+    }
+    return e;
 }
 
 // Deterministic FP64 sum of n values in one block (fixed order).
@@ -227,6 +275,12 @@ __global__ void k_fill_d(double *p, long long n, double v) {
 }  // namespace
 
 lbm_status lbm_check_status(lbm_melt *h) { return check_status(h); }
+
+void lbm_jmax_invalidate(lbm_melt *h) {
+    h->ab_known = -1;
+    h->jmax_pending = 0;
+    h->jmax_stale = 1;
+}
 
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
 
@@ -319,8 +373,12 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         {(void **)&h->nb[0], nc * 4}, {(void **)&h->nb[1], nc * 4},
         {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
         {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
-        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 6 * 8}};
+        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 6 * 8},
+        {(void **)&h->jmax_dev, sizeof(int)}};
     h->nred = kRedBlocks;
+    h->ab_known = -1;
+    if (cudaMallocHost(&h->jmax_host, sizeof(int)) != cudaSuccess) return fail(LBM_ENOMEM);
+    if (cudaEventCreateWithFlags(&h->jmax_ev, cudaEventDisableTiming) != cudaSuccess) return fail(LBM_ECUDA);
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.b);
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
@@ -346,6 +404,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[1], 0, nc * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->gpost, 0, 7 * nc * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) {
         k_fill_d<<<nb, 256, 0, h->stream>>>(h->s[0], (long long)nc, d.s0);
         k_fill_f<<<nb, 256, 0, h->stream>>>(h->thw_cur, (long long)nc, (float)Th);
@@ -386,8 +445,15 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
     if (!h) return LBM_EINVAL;
     if (n < 0) return set_err(h, LBM_EINVAL, "negative step count");
     const dim3 blk = h->bx ? dim3(h->bx, h->by, 1) : lbm::node_block(h->kp);
+    if (n > 0 && h->jmax_stale) {
+        k_jmax<<<(int)std::min<long long>(1024, (h->kp.ncols + 255) / 256), 256, 0, h->stream>>>(
+            h->js[h->cur], h->kp.ncols, h->jmax_dev);
+        CK(cudaGetLastError(), "liquid-count maximum");
+        h->jmax_stale = 0;
+    }
     for (long long t = 0; t < n; ++t) {
         Bufs b = bufs(h);
+        b.abound = axial_bound(h);
         const int odd = h->inflight;
         cudaEvent_t *evp = nullptr;
         if (h->timing) {
@@ -411,6 +477,8 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, 1, b, h->stream), "flip");
         h->cur ^= 1;
         h->steps++;
+        h->exec_steps++;
+        CK(jmax_readback(h), "liquid-count read-back");
         if (h->report_every > 0 && h->steps % h->report_every == 0) {
             double *row = h->report + 7 * (h->report_rows % h->report_cap);
             b = bufs(h);
@@ -550,8 +618,11 @@ LBM_API lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *
     if (S) {
         lbm_status st = copy_in(h, h->s[h->cur], S, nc * 8, ptr_kind);
         if (st != LBM_OK) return st;
-        // liquid counts from the new fronts, front held
+        // liquid counts from the new fronts, front held; their maximum anew
+        CK(cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream), "reset maximum");
         if ((st = refresh_front(h)) != LBM_OK) return st;
+        lbm_jmax_invalidate(h);
+        h->jmax_stale = 0;  // refresh_front recorded the new counts
     }
     const float *fd = f, *gd = g;
     float *tf = nullptr, *tg = nullptr;

@@ -103,6 +103,32 @@ def test_steps_from_random_state(lib, orc, face, nsteps):
 
 
 @pytest.mark.parametrize("face", [0, 1])
+def test_front_raised_by_set_state(lib, orc, face):
+    """The stream-collide grid stops above the liquid counts (deep solid
+    nodes do nothing): after a low front has run long enough for that bound
+    to be known, a state whose fronts lie six to twelve nodes higher must
+    still be stepped everywhere."""
+    shape = (22, 20, 18) if face == 0 else (22, 18, 20)
+    kw = dict(face=face, Ra=2e4, Pr=0.5, Ste=0.3, Ma=0.15, s0=1.5, derive=True)
+    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu.step(48)
+    gpu.sync()
+    f, g, s = _random_state(o, 41 + face, 8.0, 14.0)
+    o.set_state(f.astype(np.float64), g.astype(np.float64), s)
+    gpu.set_state(f, g, s)
+    gpu.step(25)
+    o.step(25)
+    fg, gg, sg = gpu.get_state()
+    fo, go, so = o.get_state()
+    liq = fo.any(axis=0)
+    np.testing.assert_allclose(sg, so, atol=1e-7, rtol=0)
+    # 25 steps of FP32 rounding; a node left out would be off by O(1e-2)
+    np.testing.assert_allclose(fg, fo, atol=2e-5, rtol=0)
+    np.testing.assert_allclose(gg[:, liq], go[:, liq], atol=2e-5, rtol=0)
+    _compare(gpu, o, tol_u=2e-5)
+
+
+@pytest.mark.parametrize("face", [0, 1])
 def test_flips_after_even_and_odd_steps(lib, orc, face):
     """Fronts placed just below node centres so that nodes melt in the first
     (even, values in flight) and second (odd) steps: the link rewrite of the
