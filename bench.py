@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the FP16, ensemble and adjoint legs (profiling runs)")
+    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint"],
+                    help="run one of the extra legs alone and print its JSON (profiling runs)")
+    ap.add_argument("--leg-steps", type=int, default=0, help="steps of that leg (0: its default)")
     return ap.parse_args()
 
 
@@ -73,6 +76,42 @@ def reduce_across_ranks(ms, units, dist=None, device="cpu"):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(t.item()), float(u.item())
+
+
+# Sources of the stream-collide launch (kernels, their launchers and the step
+# loop that sizes the grid): a recorded DRAM traffic figure holds only while
+# they are unchanged.
+K1_SOURCES = ("paper_1604_03478_gb300/csrc/kernels.cuh", "paper_1604_03478_gb300/csrc/lbm_core.cuh",
+              "paper_1604_03478_gb300/csrc/launch.h", "paper_1604_03478_gb300/csrc/launch_impl.cuh",
+              "paper_1604_03478_gb300/csrc/k_f32.cu", "paper_1604_03478_gb300/csrc/lbm_melt.cu")
+TRAFFIC_RECORD = "profiles/stream_collide_256cube_fp32_traffic.md"
+
+
+def k1_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in K1_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes (read + write) per stream-collide launch of the 256^3 FP32
+    workload, from the committed ncu record, or None when the record is
+    missing or the kernel sources changed since it was taken."""
+    try:
+        rec = {}
+        with open(os.path.join(ROOT, TRAFFIC_RECORD)) as f:
+            for ln in f:
+                if ":" in ln and ln.split(":", 1)[0].strip() in ("source_sha256", "bytes_per_launch"):
+                    k, v = ln.split(":", 1)
+                    rec[k.strip()] = v.strip().strip("`")
+        if rec.get("source_sha256") != k1_source_hash():
+            return None
+        return float(rec["bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def hbm_peak():
@@ -440,7 +479,8 @@ def run_gpu(args):
                    "liquid_fraction": float(np.mean(S1) / H), "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state 1.7 GB > L2 (inputs larger than L2, no flush)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "fused stream-collide (k_even/k_odd)",
+                     "traffic": recorded_traffic() if (n == N_EDGE and args.precision == 0) else None,
+                     "traffic_source": TRAFFIC_RECORD, "kernel": "fused stream-collide (k_even/k_odd)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k1_avg_ms, "peak_source": peak_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": ncols * 4,
@@ -458,10 +498,21 @@ def run_gpu(args):
     return 0
 
 
+def run_leg(args):
+    import torch
+    torch.cuda.set_device(0)
+    legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg}
+    kw = {"steps": args.leg_steps} if args.leg_steps > 0 else {}
+    print(json.dumps({"leg": args.leg, **legs[args.leg](**kw)}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_gpu(args)
 
 

@@ -46,19 +46,24 @@ struct lbm_melt {
     int timing;
     int bx, by;        // block shape of the per-node kernels (0: default)
     int cblk;          // threads per block of the per-column kernels
-    // Height bound of the stream-collide grid (solid nodes two above every
-    // liquid count of their neighbourhood do nothing): k_front keeps a
-    // running maximum of the liquid counts on the device, read back
-    // asynchronously every few steps; a count grows by at most one a step.
+    int sms;           // SMs of the device
+    // Running maximum of the liquid counts, kept by k_front on the device;
+    // stream-collide blocks at heights >= it + 3 (all deep solid) return at
+    // once.  It is also copied every kRbEvery steps into a ring of pinned
+    // slots; before a stream-collide the host takes the newest copy at least
+    // kRbLag steps old (waiting for it only when it runs that far ahead of
+    // the device) and launches no block above it + its age + 2 (a count
+    // grows by at most one node per step).
+    static const int kRbRing = 32, kRbLag = 16, kRbEvery = 4;
     int *jmax_dev;
-    int *jmax_host;    // pinned landing slot of the read-back
-    cudaEvent_t jmax_ev;
-    int jmax_pending;  // a read-back is in flight
-    int jmax_stale;    // jmax_dev may be below the counts (advanced elsewhere)
-    long long jmax_pending_at;  // exec_steps when it was enqueued
-    int ab_known;      // last maximum read, -1: unknown
-    long long ab_at;   // exec_steps at which ab_known held
-    long long exec_steps;  // steps this handle executed (never rewound)
+    int jmax_stale;    // jmax_dev may be below the counts (state advanced elsewhere)
+    int *rb_val;       // pinned ring of read-backs
+    cudaEvent_t rb_ev[kRbRing];
+    long long rb_step[kRbRing];  // exec step after which each copy was taken
+    long long rb_next;           // read-backs enqueued so far
+    long long rb_valid_from;     // read-backs before this one are not bounds any more
+    long long rb_synced;         // newest read-back known complete (its value read)
+    long long exec_steps;        // steps this handle executed (never rewound)
     double Ra;         // as given to create
     int derived_from_Ra;
     void *tape;        // recorded run for the adjoint (adjoint.cu)
@@ -73,6 +78,7 @@ void lbm_tape_free(lbm_melt *h);
 // LBM_EUNSTABLE after a step with |ds| > 1/2, LBM_ENAN after a non-finite
 // front temperature, else LBM_OK.
 lbm_status lbm_check_status(lbm_melt *h);
-// Forget the host's view of the liquid-count maximum: after the state was
-// advanced by other code (the ensemble) or replaced.
+// Mark the running maximum of the liquid counts stale (the state was
+// advanced by code that does not keep it: the ensemble); the next step
+// recomputes it first.
 void lbm_jmax_invalidate(lbm_melt *h);

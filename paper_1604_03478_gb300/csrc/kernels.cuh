@@ -95,15 +95,34 @@ __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *_
     for (int i = 0; i < 7; ++i) Store<ST>::st(G + opp7(i) * p.ld + c, g[i]);
 }
 
+// Stream-collide grid: blocks of blockDim.x x blockDim.y nodes of one plane
+// across the heating axis, with the height along that axis slowest
+// (blockIdx.z), so that the blocks near the heated wall are dispatched
+// first.  jmax (null: no bound) is the running maximum of the liquid counts,
+// written by the previous front update: nodes two or more above every
+// neighbouring count are deep solid and do nothing, so a block whose heights
+// are all >= jmax + 3 returns at once.
+template <int FACE>
+__device__ __forceinline__ bool k1_node(const KP &p, const int *jmax, int &x, int &y, int &z) {
+    const int a0 = (int)blockIdx.z * (FACE == 0 ? (int)blockDim.y : 1);  // lowest height of the block
+    if (jmax && a0 >= *jmax + 3) return false;
+    x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (FACE == 0) {
+        y = a0 + (int)threadIdx.y;
+        z = (int)blockIdx.y;
+    } else {
+        y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
+        z = (int)blockIdx.z;
+    }
+    return x < p.nx && y < p.ny;
+}
+
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const int *__restrict__ nb,
-                                              const float *__restrict__ gpost) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
-    even_node<ST, FACE>(p, F, G, js, nb, gpost, x, y, z);
+                                              const float *__restrict__ gpost, const int *jmax) {
+    int x, y, z;
+    if (k1_node<FACE>(p, jmax, x, y, z)) even_node<ST, FACE>(p, F, G, js, nb, gpost, x, y, z);
 }
 
 
@@ -213,12 +232,10 @@ template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_odd(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                              const int *__restrict__ js, const int *__restrict__ nb,
                                              const float *__restrict__ gpost, const float *__restrict__ thw_rd,
-                                             const float *__restrict__ thw_wr, const __grid_constant__ Links lk) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
-    odd_node<ST, FACE>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+                                             const float *__restrict__ thw_wr, const __grid_constant__ Links lk,
+                                             const int *jmax) {
+    int x, y, z;
+    if (k1_node<FACE>(p, jmax, x, y, z)) odd_node<ST, FACE>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
 }
 
 

@@ -22,7 +22,7 @@ struct Bufs {
     const Links *lk;             // interior link offsets of the odd step
     int cblk;                    // threads per block of the per-column kernels (col_block)
     int *jmax;                   // running maximum of the liquid counts (k_front), or null
-    int abound;                  // stream-collide covers heights < abound only (all above are deep solid)
+    int k1_height;               // the stream-collide grid covers heights < k1_height (the rest is deep solid)
 };
 
 template <typename ST> struct Launch {
@@ -56,6 +56,18 @@ inline dim3 node_block(const KP &p) {
 inline dim3 node_grid(const KP &p, dim3 b) {
     return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
 }
+// Grid of the stream-collide (k1_node): x tiles, the in-plane tiles, then
+// the heights along the heating axis (slowest).
+inline dim3 k1_grid(const KP &p, dim3 b, int face, int height) {
+    const unsigned gx = (p.nx + b.x - 1) / b.x;
+    if (height < 1) height = 1;
+    if (face == 0) {
+        const unsigned gz = (unsigned)((height + (int)b.y - 1) / (int)b.y), full = (p.ny + b.y - 1) / b.y;
+        return dim3(gx, p.nz, gz < full ? gz : full);
+    }
+    return dim3(gx, (p.ny + b.y - 1) / b.y, (unsigned)(height < p.nz ? height : p.nz));
+}
+
 // node_grid cut to the heights a < abound along the heating axis (y for
 // face 0, z for face 1).
 inline dim3 node_grid_axial(const KP &p, dim3 b, int face, int abound) {

@@ -9,14 +9,15 @@ namespace lbm {
 
 template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
-    const dim3 grd = node_grid_axial(p, blk, face, b.abound);
+    const dim3 grd = k1_grid(p, blk, face, b.k1_height);
+    const int *jm = p.skip_deep ? b.jmax : nullptr;
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk);
-        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
+        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
-        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk);
-        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost);
+        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
     }
     return cudaGetLastError();
 }

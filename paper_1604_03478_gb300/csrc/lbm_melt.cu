@@ -154,7 +154,7 @@ Bufs bufs(lbm_melt *h) {
     b.lk = &h->lk;
     b.cblk = h->cblk;
     b.jmax = h->jmax_dev;
-    b.abound = h->kp.H;
+    b.k1_height = h->kp.H;
     return b;
 }
 
@@ -200,8 +200,9 @@ void free_all(lbm_melt *h) {
     cudaFree(h->totals_dev);
     cudaFree(h->report);
     cudaFree(h->jmax_dev);
-    if (h->jmax_host) cudaFreeHost(h->jmax_host);
-    if (h->jmax_ev) cudaEventDestroy(h->jmax_ev);
+    if (h->rb_val) cudaFreeHost(h->rb_val);
+    for (int k = 0; k < lbm_melt::kRbRing; ++k)
+        if (h->rb_ev[k]) cudaEventDestroy(h->rb_ev[k]);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
 }
@@ -215,37 +216,40 @@ __global__ void k_jmax(const int *__restrict__ js, long long n, int *__restrict_
     if ((threadIdx.x & 31) == 0 && m >= 0) atomicMax(jmax, m);
 }
 
-// Height bound for the next stream-collide: all heights when deep solid
-// nodes are updated (Tc below Tm) or while the maximum is unknown.
-int axial_bound(lbm_melt *h) {
+// Height bound of the next stream-collide grid (see lbm_melt::kRbLag): all
+// heights while no valid read-back old enough exists, or when deep solid
+// nodes are updated (Tc below Tm).
+lbm_status k1_height(lbm_melt *h, int *out) {
     const int H = h->kp.H;
-    if (!h->kp.skip_deep) return H;
-    if (h->jmax_pending) {
-        const cudaError_t e = cudaEventQuery(h->jmax_ev);
-        if (e == cudaSuccess) {
-            h->ab_known = *h->jmax_host;
-            h->ab_at = h->jmax_pending_at;
-            h->jmax_pending = 0;
-        } else if (e == cudaErrorNotReady) {
-            (void)cudaGetLastError();  // not an error: the copy is still in flight
+    *out = H;
+    if (!h->kp.skip_deep || h->jmax_stale) return LBM_OK;
+    const long long want = h->exec_steps - lbm_melt::kRbLag;
+    const long long oldest = std::max(h->rb_valid_from, h->rb_next - lbm_melt::kRbRing);
+    for (long long k = h->rb_next - 1; k >= oldest; --k) {
+        const int slot = (int)(k % lbm_melt::kRbRing);
+        if (h->rb_step[slot] > want) continue;
+        if (k > h->rb_synced) {
+            CK(cudaEventSynchronize(h->rb_ev[slot]), "read-back wait");
+            h->rb_synced = k;
         }
+        // the copy followed step rb_step (0-based): counts of the state the
+        // coming step reads exceed it by at most the steps in between
+        const long long b = (long long)h->rb_val[slot] + (h->exec_steps - h->rb_step[slot] - 1) + 3;
+        *out = b < H ? (int)b : H;
+        return LBM_OK;
     }
-    if (h->ab_known < 0) return H;
-    const long long b = (long long)h->ab_known + (h->exec_steps - h->ab_at) + 3;
-    return b < H ? (int)b : H;
+    return LBM_OK;
 }
 
-// After a step: enqueue a read-back of the running maximum every 16 steps.
-cudaError_t jmax_readback(lbm_melt *h) {
-    if (!h->kp.skip_deep || h->jmax_pending) return cudaSuccess;
-    if (h->ab_known >= 0 && h->exec_steps - h->ab_at < 16) return cudaSuccess;
-    cudaError_t e = cudaMemcpyAsync(h->jmax_host, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(h->jmax_ev, h->stream);
-    if (e == cudaSuccess) {
-        h->jmax_pending = 1;
-        h->jmax_pending_at = h->exec_steps;
-    }
-    return e;
+// After every kRbEvery-th step: copy the running maximum into the next ring slot.
+lbm_status jmax_readback(lbm_melt *h) {
+    if (!h->kp.skip_deep || h->exec_steps % lbm_melt::kRbEvery) return LBM_OK;
+    const int slot = (int)(h->rb_next % lbm_melt::kRbRing);
+    CK(cudaMemcpyAsync(h->rb_val + slot, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read-back");
+    CK(cudaEventRecord(h->rb_ev[slot], h->stream), "read-back event");
+    h->rb_step[slot] = h->exec_steps - 1;
+    h->rb_next++;
+    return LBM_OK;
 }
 
 // Deterministic FP64 sum of n values in one block (fixed order).
@@ -277,9 +281,8 @@ __global__ void k_fill_d(double *p, long long n, double v) {
 lbm_status lbm_check_status(lbm_melt *h) { return check_status(h); }
 
 void lbm_jmax_invalidate(lbm_melt *h) {
-    h->ab_known = -1;
-    h->jmax_pending = 0;
     h->jmax_stale = 1;
+    h->rb_valid_from = h->rb_next;
 }
 
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
@@ -364,7 +367,12 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1)
             return fail(LBM_ECUDA);
         h->cblk = lbm::col_block(h->kp.ncols, sms);
+        h->sms = sms;
     }
+    h->rb_synced = -1;
+    if (cudaMallocHost(&h->rb_val, lbm_melt::kRbRing * sizeof(int)) != cudaSuccess) return fail(LBM_ENOMEM);
+    for (int k = 0; k < lbm_melt::kRbRing; ++k)
+        if (cudaEventCreateWithFlags(&h->rb_ev[k], cudaEventDisableTiming) != cudaSuccess) return fail(LBM_ECUDA);
     const size_t es = h->precision == 1 ? sizeof(__half) : sizeof(float);
     const size_t nF = 19 * (size_t)p.ld * es, nG = 7 * (size_t)p.ld * es;
     const size_t nc = (size_t)d.ncols;
@@ -376,9 +384,6 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 6 * 8},
         {(void **)&h->jmax_dev, sizeof(int)}};
     h->nred = kRedBlocks;
-    h->ab_known = -1;
-    if (cudaMallocHost(&h->jmax_host, sizeof(int)) != cudaSuccess) return fail(LBM_ENOMEM);
-    if (cudaEventCreateWithFlags(&h->jmax_ev, cudaEventDisableTiming) != cudaSuccess) return fail(LBM_ECUDA);
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.b);
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
@@ -453,7 +458,8 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
     }
     for (long long t = 0; t < n; ++t) {
         Bufs b = bufs(h);
-        b.abound = axial_bound(h);
+        lbm_status hs = k1_height(h, &b.k1_height);
+        if (hs != LBM_OK) return hs;
         const int odd = h->inflight;
         cudaEvent_t *evp = nullptr;
         if (h->timing) {
@@ -478,7 +484,7 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         h->cur ^= 1;
         h->steps++;
         h->exec_steps++;
-        CK(jmax_readback(h), "liquid-count read-back");
+        if ((hs = jmax_readback(h)) != LBM_OK) return hs;
         if (h->report_every > 0 && h->steps % h->report_every == 0) {
             double *row = h->report + 7 * (h->report_rows % h->report_cap);
             b = bufs(h);
@@ -621,8 +627,8 @@ LBM_API lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *
         // liquid counts from the new fronts, front held; their maximum anew
         CK(cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream), "reset maximum");
         if ((st = refresh_front(h)) != LBM_OK) return st;
-        lbm_jmax_invalidate(h);
-        h->jmax_stale = 0;  // refresh_front recorded the new counts
+        h->rb_valid_from = h->rb_next;  // earlier copies may lie below the new counts
+        h->jmax_stale = 0;              // refresh_front recorded them
     }
     const float *fd = f, *gd = g;
     float *tf = nullptr, *tg = nullptr;
