@@ -741,7 +741,7 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     // maximum; the snapshot and the node adjoint touch nothing three or more
     // nodes above it (deep solid), so their grids stop there.
     int abound = p.H;
-    if (p.skip_deep && !h->jmax_stale) {
+    if (p.skip_deep) {
         int jm = 0;
         if (cudaMemcpy(&jm, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return tape_err(h, LBM_ECUDA, "liquid-count maximum");

@@ -52,6 +52,8 @@ struct CavDesc {
     double *s[2];
     float *gpost, *thw, *thw_rd0;
     int *status;
+    int *jmax;                    // running maximum of the liquid counts (kept by phase 2)
+    int cut;                      // nodes at heights >= *jmax + 3 are deep solid (Tc == Tm)
 };
 
 // Everything the launch needs, passed as one __grid_constant__ kernel
@@ -132,38 +134,47 @@ ENS_FN void ens_odd(const CavDesc &d, int cur, const float *trd, int x, int y, i
     odd_node<ST, FACE, false>(d.p, nullptr, (ST *)d.F, (ST *)d.G, d.js[cur], d.nb[cur], d.gpost, trd, d.thw, x, y, z);
 }
 
-// One column of phase 2 (front update) or 3 (flip).
+// One column of phase 2 (front update; returns the new liquid count) or 3
+// (flip; returns -1).
 template <typename ST>
-ENS_FN void ens_column(const CavDesc &d, int cur, int inflight, int phase, int col) {
+ENS_FN int ens_column(const CavDesc &d, int cur, int inflight, int phase, int col) {
     if (phase == 2) {
         const ST *F = (const ST *)d.F, *G = (const ST *)d.G;
         if (d.face == 0)
-            front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
-                                inflight, 1, d.status, col);
-        else
-            front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
-                                inflight, 1, d.status, col);
+            return front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                       inflight, 1, d.status, col);
+        return front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+                                   inflight, 1, d.status, col);
     } else {
         ST *F = (ST *)d.F;
         if (d.face == 0) flip_column<ST, 0>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
         else flip_column<ST, 1>(d.p, F, d.js[cur], d.js[1 - cur], d.nb[1 - cur], inflight, 1, col);
+        return -1;
     }
 }
 
 template <typename ST, int K>
 __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_constant__ EnsWork w, int nsteps) {
     const long long items1 = w.item_begin[w.ncav], items2 = w.col_begin[w.ncav];
+    __shared__ int top[kMaxCavities];  // per cavity: first height at which every node is deep solid
     for (int t = 0; t < nsteps; ++t) {
+        for (int k = threadIdx.x; k < w.ncav; k += blockDim.x) {
+            const CavDesc &d = w.desc[k];
+            top[k] = d.cut ? *(volatile int *)d.jmax + 3 : 1 << 30;
+        }
+        __syncthreads();
         // phase 1: fused stream-collide of every node of every cavity; an
-        // item is one (1 << bxs) x by tile of K consecutive z-planes
+        // item is one (1 << bxs) x by tile of K consecutive z-planes; tiles
+        // wholly above the liquid (deep solid) are skipped
         for (long long it = blockIdx.x; it < items1; it += gridDim.x) {
             const int k = find_cavity(w.item_begin, w.ncav, it);
             const CavDesc &d = w.desc[k];
-            const int cur = d.cur0 ^ (t & 1), odd = d.inflight0 ^ (t & 1);
-            const float *trd = t == 0 ? d.thw_rd0 : d.thw;
             const int li = (int)(it - w.item_begin[k]);
             const int zc = li / d.gxy, r = li - zc * d.gxy;
             const int iy = r / d.gx, ix = r - iy * d.gx;
+            if ((d.face == 0 ? iy * d.by : zc * K) >= top[k]) continue;
+            const int cur = d.cur0 ^ (t & 1), odd = d.inflight0 ^ (t & 1);
+            const float *trd = t == 0 ? d.thw_rd0 : d.thw;
             const int x = (ix << d.bxs) + (threadIdx.x & ((1 << d.bxs) - 1));
             const int y = iy * d.by + (threadIdx.x >> d.bxs);
             if (x >= d.p.nx || y >= d.p.ny) continue;
@@ -188,7 +199,11 @@ __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_con
                 const CavDesc &d = w.desc[k];
                 const int cur = d.cur0 ^ (t & 1), inflight = 1 - (d.inflight0 ^ (t & 1));
                 const int col = (int)((it - w.col_begin[k]) * blockDim.x + threadIdx.x);
-                if (col < d.p.ncols) ens_column<ST>(d, cur, inflight, phase, col);
+                const int jn = col < d.p.ncols ? ens_column<ST>(d, cur, inflight, phase, col) : -1;
+                if (phase == 2) {  // an item is one cavity's columns: whole warps
+                    const int m = __reduce_max_sync(0xffffffffu, jn);
+                    if ((threadIdx.x & 31) == 0 && m >= 0) atomicMax(d.jmax, m);
+                }
             }
             if (!grid_barrier(w, gridDim.x)) return;
         }
@@ -275,6 +290,8 @@ void fill_desc(lbm_melt *h, CavDesc &d, int block) {
     d.thw = h->thw_cur;
     d.thw_rd0 = h->thw_pending ? h->thw_prev : h->thw_cur;
     d.status = h->status_dev;
+    d.jmax = h->jmax_dev;
+    d.cut = h->kp.skip_deep;
 }
 
 // Work-list prefix sums and the co-resident grid for the launch shape.
@@ -348,7 +365,7 @@ void advance_handles(lbm_ensemble *e, long long n) {
         h->steps += n;
         if (n & 1) { h->cur ^= 1; h->inflight ^= 1; }
         if (n > 0) h->thw_pending = 0;
-        if (n > 0) lbm_jmax_invalidate(h);  // its fronts moved without the running maximum
+        h->exec_steps += n;  // the launch kept the running maximum: host read-backs stay bounds
     }
     e->steps += n;
 }

@@ -56,7 +56,6 @@ struct lbm_melt {
     // grows by at most one node per step).
     static const int kRbRing = 32, kRbLag = 16, kRbEvery = 4;
     int *jmax_dev;
-    int jmax_stale;    // jmax_dev may be below the counts (state advanced elsewhere)
     int *rb_val;       // pinned ring of read-backs
     cudaEvent_t rb_ev[kRbRing];
     long long rb_step[kRbRing];  // exec step after which each copy was taken
@@ -78,7 +77,4 @@ void lbm_tape_free(lbm_melt *h);
 // LBM_EUNSTABLE after a step with |ds| > 1/2, LBM_ENAN after a non-finite
 // front temperature, else LBM_OK.
 lbm_status lbm_check_status(lbm_melt *h);
-// Mark the running maximum of the liquid counts stale (the state was
-// advanced by code that does not keep it: the ensemble); the next step
-// recomputes it first.
-void lbm_jmax_invalidate(lbm_melt *h);
+

@@ -207,22 +207,13 @@ void free_all(lbm_melt *h) {
     h->ev.clear();
 }
 
-// Running maximum of js over n columns into *jmax (one atomic per warp).
-__global__ void k_jmax(const int *__restrict__ js, long long n, int *__restrict__ jmax) {
-    int m = -1;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        m = max(m, js[i]);
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m >= 0) atomicMax(jmax, m);
-}
-
 // Height bound of the next stream-collide grid (see lbm_melt::kRbLag): all
 // heights while no valid read-back old enough exists, or when deep solid
 // nodes are updated (Tc below Tm).
 lbm_status k1_height(lbm_melt *h, int *out) {
     const int H = h->kp.H;
     *out = H;
-    if (!h->kp.skip_deep || h->jmax_stale) return LBM_OK;
+    if (!h->kp.skip_deep) return LBM_OK;
     const long long want = h->exec_steps - lbm_melt::kRbLag;
     const long long oldest = std::max(h->rb_valid_from, h->rb_next - lbm_melt::kRbRing);
     for (long long k = h->rb_next - 1; k >= oldest; --k) {
@@ -280,10 +271,7 @@ __global__ void k_fill_d(double *p, long long n, double v) {
 
 lbm_status lbm_check_status(lbm_melt *h) { return check_status(h); }
 
-void lbm_jmax_invalidate(lbm_melt *h) {
-    h->jmax_stale = 1;
-    h->rb_valid_from = h->rb_next;
-}
+
 
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
 
@@ -450,12 +438,6 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
     if (!h) return LBM_EINVAL;
     if (n < 0) return set_err(h, LBM_EINVAL, "negative step count");
     const dim3 blk = h->bx ? dim3(h->bx, h->by, 1) : lbm::node_block(h->kp);
-    if (n > 0 && h->jmax_stale) {
-        k_jmax<<<(int)std::min<long long>(1024, (h->kp.ncols + 255) / 256), 256, 0, h->stream>>>(
-            h->js[h->cur], h->kp.ncols, h->jmax_dev);
-        CK(cudaGetLastError(), "liquid-count maximum");
-        h->jmax_stale = 0;
-    }
     for (long long t = 0; t < n; ++t) {
         Bufs b = bufs(h);
         lbm_status hs = k1_height(h, &b.k1_height);
@@ -628,7 +610,6 @@ LBM_API lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *
         CK(cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream), "reset maximum");
         if ((st = refresh_front(h)) != LBM_OK) return st;
         h->rb_valid_from = h->rb_next;  // earlier copies may lie below the new counts
-        h->jmax_stale = 0;              // refresh_front recorded them
     }
     const float *fd = f, *gd = g;
     float *tf = nullptr, *tg = nullptr;
