@@ -86,13 +86,13 @@ __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *_
         for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(G + i * p.ld + c);
         collide(p, f, g);
 #pragma unroll
-        for (int i = 0; i < 19; ++i) Store<ST>::st(F + opp(i) * p.ld + c, f[i]);
+        for (int i = 0; i < 19; ++i) Store<ST>::st_stream(F + opp(i) * p.ld + c, f[i]);
     } else {
         if (deep_solid(p, a, __ldg(nb + col))) return;
         solid_post(p, a == jsc, gpost, col, g);
     }
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<ST>::st(G + opp7(i) * p.ld + c, g[i]);
+    for (int i = 0; i < 7; ++i) Store<ST>::st_stream(G + opp7(i) * p.ld + c, g[i]);
 }
 
 // Stream-collide grid: blocks of blockDim.x x blockDim.y nodes of one plane
@@ -204,26 +204,26 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
         collide(p, f, g);
         if (interior) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) Store<ST>::st(Fc + fout_off<FACE, TAB>(p, lk, i), f[i]);
+            for (int i = 0; i < 19; ++i) Store<ST>::st_stream(Fc + fout_off<FACE, TAB>(p, lk, i), f[i]);
 #pragma unroll
-            for (int i = 0; i < 7; ++i) Store<ST>::st(Gc + gout_off<FACE, TAB>(p, lk, i), g[i]);
+            for (int i = 0; i < 7; ++i) Store<ST>::st_stream(Gc + gout_off<FACE, TAB>(p, lk, i), g[i]);
             return;
         }
-        Store<ST>::st(Fc, f[0]);
+        Store<ST>::st_stream(Fc, f[0]);
 #pragma unroll
         for (int i = 1; i < 19; ++i)
-            Store<ST>::st(((lm >> opp(i)) & 1u) ? Fc + fout_off<FACE, TAB>(p, lk, i) : Fc + opp(i) * p.ld, f[i]);
+            Store<ST>::st_stream(((lm >> opp(i)) & 1u) ? Fc + fout_off<FACE, TAB>(p, lk, i) : Fc + opp(i) * p.ld, f[i]);
     } else {
         if (deep_solid(p, a, nbv)) return;
         solid_post(p, a == jsc, gpost, col, g);
     }
     const unsigned im = off_walls ? 0x7eu : inside_mask(p, x, y, z);
     const float th_wr = __ldg(thw_wr + col);
-    Store<ST>::st(Gc, g[0]);
+    Store<ST>::st_stream(Gc, g[0]);
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
         const bool out = (im >> opp7(i)) & 1u;
-        Store<ST>::st(out ? Gc + gout_off<FACE, TAB>(p, lk, i) : Gc + opp7(i) * p.ld,
+        Store<ST>::st_stream(out ? Gc + gout_off<FACE, TAB>(p, lk, i) : Gc + opp7(i) * p.ld,
                       out ? g[i] : wall_value<FACE>(p, i, g[i], th_wr));
     }
 }

@@ -122,13 +122,17 @@ struct Links {
 
 // ------------------------------------------------------------ load/store
 template <typename ST> struct Store;
+// st_stream: a store of the stream-collide, marked evict-first (the state is
+// far larger than L2 and is next read a whole step later).
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st_stream(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
 };
 
 // ----------------------------------------------- compile-time transforms
