@@ -302,7 +302,7 @@ def precision_leg(steps=200, twin_steps=400):
     return out
 
 
-def ensemble_leg(steps=20, n_cav=48, seed=2016):
+def ensemble_leg(steps=100, n_cav=48, seed=2016):
     """48 seeded cavities of uneven sizes in one persistent launch per run of
     steps, against the same cavities stepped one after another."""
     import torch

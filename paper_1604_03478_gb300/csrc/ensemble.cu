@@ -24,6 +24,7 @@
 #include "../../include/lbm_melt.h"
 #include "handle.h"
 #include "kernels.cuh"
+#include "launch.h"
 
 #define LBM_API extern "C" __attribute__((visibility("default")))
 
@@ -267,11 +268,11 @@ const void *kernel_ptr(int precision, int K) {
     return (const void *)lbm::k_ensemble<float, 4>;
 }
 
-// Tile of a cavity for the block size: as wide along x as the row needs (a
-// power of two, at least 32), the rest of the block along y.
+// Tile of a cavity for the block size: a power of two from 32 to 128 wide
+// along x, the one that leaves the fewest idle lanes over a row
+// (block_width), the rest of the block along y.
 void tile(const lbm::KP &p, int block, int &bxs, int &by) {
-    int bx = 32;
-    while (bx < p.nx && bx < block) bx *= 2;
+    const int bx = lbm::block_width(p.nx, block);
     bxs = 0;
     while ((1 << bxs) < bx) ++bxs;
     by = block / bx;

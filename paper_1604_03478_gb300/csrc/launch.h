@@ -49,8 +49,23 @@ inline int col_block(long long ncols, int sms) {
 inline dim3 col_grid(long long ncols, int b) { return dim3((unsigned)((ncols + b - 1) / b)); }
 
 // Block shape for the per-node kernels: 128 threads, x-major.
+// Width along x of a block of `block` threads: the power of two from 32 to
+// min(block, 128) that leaves the fewest idle lanes over a row of nx nodes
+// (the widest on a tie): 160 -> 32, 96 -> 32, 48 -> 64, 256 -> 128.
+inline int block_width(int nx, int block) {
+    int best = 32;
+    long long best_waste = -1;
+    for (int bx = 32; bx <= block && bx <= 128; bx *= 2) {
+        const long long waste = (long long)((nx + bx - 1) / bx) * bx - nx;
+        if (best_waste < 0 || waste <= best_waste) {
+            best = bx;
+            best_waste = waste;
+        }
+    }
+    return best;
+}
 inline dim3 node_block(const KP &p) {
-    int bx = p.nx >= 128 ? 128 : (p.nx > 64 ? 128 : (p.nx > 32 ? 64 : 32));
+    const int bx = block_width(p.nx, 128);
     return dim3(bx, 128 / bx, 1);
 }
 inline dim3 node_grid(const KP &p, dim3 b) {

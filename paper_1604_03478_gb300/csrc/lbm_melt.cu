@@ -218,7 +218,7 @@ lbm_status k1_height(lbm_melt *h, int *out) {
     const long long oldest = std::max(h->rb_valid_from, h->rb_next - lbm_melt::kRbRing);
     for (long long k = h->rb_next - 1; k >= oldest; --k) {
         const int slot = (int)(k % lbm_melt::kRbRing);
-        if (h->rb_step[slot] > want) continue;
+        if (h->rb_step[slot] > want && k > h->rb_synced) continue;  // too recent to wait for
         if (k > h->rb_synced) {
             CK(cudaEventSynchronize(h->rb_ev[slot]), "read-back wait");
             h->rb_synced = k;
@@ -229,6 +229,19 @@ lbm_status k1_height(lbm_melt *h, int *out) {
         *out = b < H ? (int)b : H;
         return LBM_OK;
     }
+    return LBM_OK;
+}
+
+// A read-back taken now, synchronously (after create and set_state, so that
+// the first steps of a run are bounded too).
+lbm_status seed_readback(lbm_melt *h) {
+    if (!h->kp.skip_deep) return LBM_OK;
+    const int slot = (int)(h->rb_next % lbm_melt::kRbRing);
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    CK(cudaMemcpy(h->rb_val + slot, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost), "read-back");
+    h->rb_step[slot] = h->exec_steps - 1;
+    h->rb_synced = h->rb_next;
+    h->rb_next++;
     return LBM_OK;
 }
 
@@ -420,6 +433,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(Tprof_dev);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    if (seed_readback(h) != LBM_OK) return fail(LBM_ECUDA);
     *out = h;
     return LBM_OK;
 }
@@ -610,6 +624,7 @@ LBM_API lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *
         CK(cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream), "reset maximum");
         if ((st = refresh_front(h)) != LBM_OK) return st;
         h->rb_valid_from = h->rb_next;  // earlier copies may lie below the new counts
+        if ((st = seed_readback(h)) != LBM_OK) return st;
     }
     const float *fd = f, *gd = g;
     float *tf = nullptr, *tg = nullptr;
