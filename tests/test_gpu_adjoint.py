@@ -100,6 +100,23 @@ def test_gradient_vs_central_differences(lib, orc):
     cav.close()
 
 
+def test_fp16_storage_gradient(lib):
+    """Shifted FP16 storage (FP32 arithmetic): the recorded run and its
+    snapshots are FP16-rounded, the adjoint itself is FP32; the gradient stays
+    within the 1e-3 relative bar of the FP32-storage one."""
+    out = {}
+    for prec in (0, 1):
+        cav = lib(*SHAPES[0], precision=prec, derive=True, **CASES[0])
+        cav.set_hot_wall(np.full(cav.ncols, 1.0, np.float32))
+        cav.tape_forward(STEPS, 8)
+        out[prec] = cav.tape_backward(_lf_seed(None, cav))
+        cav.close()
+    (d32, p32), (d16, p16) = out[0], out[1]
+    assert p16["Ra"] == pytest.approx(p32["Ra"], rel=REL)
+    v = inputs.gaussian_field(d32.size, 1.0, 100)
+    assert float(d16.ravel() @ v) == pytest.approx(float(d32.ravel() @ v), rel=REL)
+
+
 def test_checkpoint_spacing_does_not_change_the_gradient(lib):
     out = [_gpu(lib, 0, _lf_seed, ckpt=c) for c in (1, 7, STEPS)]
     for cav, S, dth, par in out[1:]:

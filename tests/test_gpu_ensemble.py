@@ -54,6 +54,25 @@ def test_ensemble_matches_single_cavities(pkg, shape):
     ens.close()
 
 
+def test_fp16_ensemble_matches_single_cavities(pkg):
+    """Shifted FP16 storage in the batched form: members agree with FP16
+    single-cavity runs to FP32 rounding of the stored values."""
+    cases = [dict(c, precision=1) for c in CASES[:2]]
+    ens = pkg.Ensemble(cases)
+    ens.step(37)
+    ens.sync()
+    for k, c in enumerate(cases):
+        single = _single(pkg, c)
+        single.step(37)
+        a = ens.member(k).get()
+        b = single.get()
+        np.testing.assert_allclose(a[0], b[0], atol=1e-5, rtol=0)
+        np.testing.assert_allclose(a[1], b[1], atol=1e-5, rtol=0)
+        np.testing.assert_allclose(a[2], b[2], atol=1e-6, rtol=0)
+        single.close()
+    ens.close()
+
+
 def test_ensemble_against_oracle(pkg, orc):
     ens = pkg.Ensemble(CASES)
     ens.step(60)
