@@ -29,10 +29,10 @@
 #define LBM_API extern "C" __attribute__((visibility("default")))
 
 // Launch-bound occupancy target of the persistent kernel (blocks of 256
-// per SM: 3 caps it at 80 registers a thread) and whether the node variants
-// are out-of-line functions.  Measured on the 48-cavity workload: 2 blocks
-// (128 registers) 8.9 k MLUPS, 3 blocks 9.9 k, 4 blocks (64 registers) 9.3 k,
-// 1 block 7.9 k.
+// per SM: 3 caps it at 80 registers a thread, with under 100 bytes of
+// spills) and whether the node variants are out-of-line functions.  Measured
+// on the 48-cavity workload over 100 steps: 3 blocks 14.5 k MLUPS, 2 blocks
+// (up to 128 registers, no spills) 13.3 k.
 #ifndef LBM_ENS_MINB
 #define LBM_ENS_MINB 3
 #endif
@@ -145,9 +145,9 @@ ENS_FN int ens_column(const CavDesc &d, int cur, int inflight, int phase, int co
     if (phase == 2) {
         const ST *F = (const ST *)d.F, *G = (const ST *)d.G;
         if (d.face == 0)
-            return front_column<ST, 0>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+            return front_column<ST, 0, false>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
                                        inflight, 1, d.status, col);
-        return front_column<ST, 1>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
+        return front_column<ST, 1, false>(d.p, F, G, d.js[cur], d.js[1 - cur], d.s[cur], d.s[1 - cur], d.gpost, d.thw,
                                    inflight, 1, d.status, col);
     } else {
         ST *F = (ST *)d.F;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_con
             const int x = (ix << d.bxs) + (threadIdx.x & ((1 << d.bxs) - 1));
             const int y = iy * d.by + (threadIdx.x >> d.bxs);
             if (x >= d.p.nx || y >= d.p.ny) continue;
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < K; ++j) {
                 const int z = zc * K + j;
                 if (z >= d.p.nz) break;

@@ -341,7 +341,9 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // clamped to [1/2, H], its liquid-node count, and the ghost node of the new
 // front: g*_ghost = g^eq(T_ghost, 0) + (g*_L - g^eq(T_L, u_L)).
 // move = 0 keeps the front (used to prepare the ghost after a state upload).
-template <typename ST, int FACE>
+// SPEC: load the ghost's likely source node together with the gradient
+// stencil (two dependent load rounds instead of three; more registers).
+template <typename ST, int FACE, bool SPEC = true>
 __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
                                            const int *__restrict__ js, int *__restrict__ js_next,
                                            const double *__restrict__ s, double *__restrict__ s_next,
@@ -356,7 +358,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     const double Tw = (double)thw[col];
     const int jsc = js[col];
     int js9[9];
-    if (infl) load_js9(p, js, pp, q, js9);
+    if (SPEC && infl) load_js9(p, js, pp, q, js9);
     double sp = 0.0, sq = 0.0;
     if (move) {
         sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
@@ -372,7 +374,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
         if (k >= 1) y0 = node_T<ST, FACE>(p, G, col, k - 1, infl, thw);
     }
     const int L = jsc - 1;
-    const bool spec = L >= 0 && jsc < H;
+    const bool spec = SPEC && L >= 0 && jsc < H;
     float gL[7], fL[19];
     if (spec) {
         int x, y, z;
