@@ -3,8 +3,9 @@
 // the melting step of Li, Yang & Zhang, arXiv:1604.03478, section 2).
 //
 // The launch walks a work list: per step, phase 1 covers every node of every
-// cavity in items of (block size x nodes per thread) consecutive nodes
-// (fused stream-collide, Eqs. 1-5), phase 2 every column of every cavity in
+// cavity in items of (block size x nodes per thread) nodes, handed out in
+// chunks from an atomic counter (fused stream-collide, Eqs. 1-5), phase 2
+// every column of every cavity in
 // items of one block (front update, Eq. 6), phase 3 the same columns (phase
 // flip).  Phases are separated by a grid-wide barrier; the launch is
 // cooperative (all blocks resident) and every barrier wait is bounded: a
@@ -31,8 +32,9 @@
 // Launch-bound occupancy target of the persistent kernel (blocks of 256
 // per SM: 3 caps it at 80 registers a thread, with under 100 bytes of
 // spills) and whether the node variants are out-of-line functions.  Measured
-// on the 48-cavity workload over 100 steps: 3 blocks 14.5 k MLUPS, 2 blocks
-// (up to 128 registers, no spills) 13.3 k.
+// on the 48-cavity workload over 100 steps (before the dynamic tile
+// distribution): 3 blocks 14.5 k MLUPS, 2 blocks (up to 128 registers, no
+// spills) 13.3 k.
 #ifndef LBM_ENS_MINB
 #define LBM_ENS_MINB 3
 #endif
@@ -70,7 +72,7 @@ struct EnsWork {
     long long item_begin[kMaxCavities + 1];  // prefix sums of node items
     long long col_begin[kMaxCavities + 1];   // prefix sums of column items
     CavDesc desc[kMaxCavities];
-    unsigned int *bar;            // {arrived, generation, timed out}
+    unsigned int *bar;            // {arrived, generation, timed out, -, item counters (2 x u64)}
     long long max_spins;
     int skip_arrival_block;       // fault injection for tests: this block never arrives (-1: none)
 };
@@ -161,16 +163,28 @@ template <typename ST, int K>
 __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_constant__ EnsWork w, int nsteps) {
     const long long items1 = w.item_begin[w.ncav], items2 = w.col_begin[w.ncav];
     __shared__ int top[kMaxCavities];  // per cavity: first height at which every node is deep solid
+    __shared__ long long next;         // first item of the block's next chunk
+    // per-step item counters (alternating), zeroed with the barrier words
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(w.bar + 4);
+    constexpr int kChunk = 2;
     for (int t = 0; t < nsteps; ++t) {
         for (int k = threadIdx.x; k < w.ncav; k += blockDim.x) {
             const CavDesc &d = w.desc[k];
             top[k] = d.cut ? *(volatile int *)d.jmax + 3 : 1 << 30;
         }
+        if (threadIdx.x == 0) next = (long long)atomicAdd(ctr + (t & 1), (unsigned long long)kChunk);
         __syncthreads();
         // phase 1: fused stream-collide of every node of every cavity; an
         // item is one (1 << bxs) x by tile of K consecutive z-planes; tiles
-        // wholly above the liquid (deep solid) are skipped
-        for (long long it = blockIdx.x; it < items1; it += gridDim.x) {
+        // wholly above the liquid (deep solid) are skipped.  Blocks take
+        // chunks of kChunk items from the step's counter (tiles differ in
+        // work: deep-solid ones are skipped), asking for the next chunk
+        // before working on the current one.
+        for (long long base = next; base < items1; base = next) {
+            __syncthreads();  // every thread has read `next`
+            if (threadIdx.x == 0) next = (long long)atomicAdd(ctr + (t & 1), (unsigned long long)kChunk);
+            const long long stop = base + kChunk < items1 ? base + kChunk : items1;
+            for (long long it = base; it < stop; ++it) {
             const int k = find_cavity(w.item_begin, w.ncav, it);
             const CavDesc &d = w.desc[k];
             const int li = (int)(it - w.item_begin[k]);
@@ -194,7 +208,12 @@ __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_con
                     else ens_even<ST, 1>(d, cur, x, y, z);
                 }
             }
+            }
+            __syncthreads();  // `next` holds the following chunk
         }
+        // the other counter serves the next step; it was last used by the
+        // step before, which every block has left
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(t + 1) & 1] = 0ull;
         if (!grid_barrier(w, gridDim.x)) return;
         // phases 2 and 3: front update (Eq. 6), then flip, of every column
         for (int phase = 2; phase <= 3; ++phase) {
@@ -357,7 +376,7 @@ lbm_status launch(lbm_ensemble *e, int nsteps, int skip_block) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t err = cudaMemsetAsync(e->bar_dev, 0, 3 * sizeof(unsigned int), e->stream);
+    cudaError_t err = cudaMemsetAsync(e->bar_dev, 0, 8 * sizeof(unsigned int), e->stream);
     if (err == cudaSuccess) err = cudaLaunchKernelExC(&cfg, kernel_ptr(e->precision, e->K), args);
     delete w;
     ECK(err, "ensemble launch");
@@ -424,7 +443,7 @@ LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *
         if (k == 0) e->precision = h->precision;
         else if (h->precision != e->precision) return fail(LBM_EINVAL);
     }
-    if (cudaMalloc(&e->bar_dev, 4 * sizeof(unsigned int)) != cudaSuccess) return fail(LBM_ENOMEM);
+    if (cudaMalloc(&e->bar_dev, 8 * sizeof(unsigned int)) != cudaSuccess) return fail(LBM_ENOMEM);
     refresh_desc(e);
     if (plan(e) != LBM_OK) return fail(LBM_ECUDA);
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) return fail(LBM_ECUDA);
