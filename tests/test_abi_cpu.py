@@ -85,7 +85,7 @@ def test_derived_parameters_match_oracle(abi, orc, Ra, Pr, Ma, H):
     assert info.alpha / H ** 2 == pytest.approx(Ma / (H * np.sqrt(3 * Ra * Pr)), rel=1e-13)
 
 
-def test_survey_config_parameters(abi):
+def test_workload_lattice_parameters(abi):
     """Lattice viscosities of the workloads (128^3, Ra 1e5, Pr 0.02, Ma 0.1:
     nu = 3.30e-3; 256^3, Ra 1e6: nu = 2.09e-3)."""
     st, i128, _ = _derive(abi, grid_kw=dict(nx=128, ny=128, nz=128), Ra=1e5, Pr=0.02, derive=True)

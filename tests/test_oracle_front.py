@@ -11,15 +11,16 @@ import pytest
 from scipy.optimize import brentq
 from scipy.special import erf
 
-SURVEY_LAMBDA = {0.05: 0.156821, 0.1: 0.220016, 0.2: 0.306424, 0.5: 0.464786, 1.0: 0.620063}
+# roots of lambda exp(lambda^2) erf(lambda) = Ste / sqrt(pi), six decimals
+TABULATED_LAMBDA = {0.05: 0.156821, 0.1: 0.220016, 0.2: 0.306424, 0.5: 0.464786, 1.0: 0.620063}
 
 
-@pytest.mark.parametrize("Ste", sorted(SURVEY_LAMBDA))
+@pytest.mark.parametrize("Ste", sorted(TABULATED_LAMBDA))
 def test_neumann_lambda(orc, Ste):
     lam = orc.neumann_lambda(Ste)
     ref = brentq(lambda l: l * np.exp(l * l) * erf(l) - Ste / np.sqrt(np.pi), 1e-9, 5, xtol=1e-15)
     assert lam == pytest.approx(ref, abs=1e-12)
-    assert lam == pytest.approx(SURVEY_LAMBDA[Ste], abs=1e-6)
+    assert lam == pytest.approx(TABULATED_LAMBDA[Ste], abs=1e-6)
 
 
 def test_neumann_lambda_small_ste(orc):
