@@ -342,7 +342,7 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // front: g*_ghost = g^eq(T_ghost, 0) + (g*_L - g^eq(T_L, u_L)).
 // move = 0 keeps the front (used to prepare the ghost after a state upload).
 // SPEC: load the ghost's likely source node together with the gradient
-// stencil (two dependent load rounds instead of three; more registers).
+// stencil (two dependent load stages instead of three; more registers).
 template <typename ST, int FACE, bool SPEC = true>
 __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
                                            const int *__restrict__ js, int *__restrict__ js_next,
@@ -352,7 +352,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     const int P1 = p.P1, P2 = p.P2, H = p.H;
     const int pp = col % P1, q = col / P1;
     const bool infl = inflight != 0;
-    // Round 1: what depends on the column only.
+    // Load stage 1: what depends on the column only.
     const double sc = s[col];
     const double Tm = p.Tm_d;
     const double Tw = (double)thw[col];
@@ -364,7 +364,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
         sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
         sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
     }
-    // Round 2: the gradient stencil of s_t and, speculatively, the node
+    // Load stage 2: the gradient stencil of s_t and, speculatively, the node
     // below the current front, which is the ghost's source node whenever the
     // liquid count does not change (all but a few columns per step).
     const int k = move ? guarded_node(sc, H) : -2;
@@ -383,7 +383,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
         if (infl) gather_f9<ST, FACE>(p, F, js9, x, y, z, L, fL);
         else gather_f<ST, FACE>(p, F, js, x, y, z, false, fL);
     }
-    // Round 3: Eq. 6.
+    // Then Eq. 6.
     double sn = sc;
     if (move) {
         double Gr;

@@ -270,6 +270,22 @@ __global__ void k_sum(const double *__restrict__ v, long long n, double scale, d
     if (threadIdx.x == 0) *out = sh[0] * scale;
 }
 
+// First pass of a two-pass FP64 sum: block b adds the b-th contiguous chunk
+// of v in a fixed order (deterministic for a given n and block count).
+__global__ void k_sum_part(const double *__restrict__ v, long long n, long long chunk, double *__restrict__ part) {
+    __shared__ double sh[256];
+    const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    double acc = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += v[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
 __global__ void k_fill_f(float *p, long long n, float v) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -563,7 +579,12 @@ LBM_API lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, doub
     if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               h->stream), "copy S");
     if (liquid_fraction) {
-        k_sum<<<1, 1024, 0, h->stream>>>(h->s[h->cur], (long long)nc, 1.0 / ((double)p.H * (double)nc), h->sum_dev);
+        // mean front height over H: two passes over the columns, chunks of
+        // at least 1024 columns per block
+        const long long nb = std::max<long long>(1, std::min<long long>(kRedBlocks, ((long long)nc + 1023) / 1024));
+        const long long chunk = ((long long)nc + nb - 1) / nb;
+        k_sum_part<<<(int)nb, 256, 0, h->stream>>>(h->s[h->cur], (long long)nc, chunk, h->red_part);
+        k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, 1.0 / ((double)p.H * (double)nc), h->sum_dev);
         CK(cudaGetLastError(), "sum");
         CK(cudaMemcpyAsync(liquid_fraction, h->sum_dev, 8,
                            ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream), "copy lf");
