@@ -1,0 +1,61 @@
+"""GPU parity at the full sizes of the benchmark workloads, in the launch
+configuration that bench.py times (default block shapes, the stream-collide
+grid cut at the height bound): the 256^3 side-heated cavity at Ra 1e6 with
+the front at 0.4 H and the 128^3 convection-melting cavity at Ra 1e5.
+
+A few steps from the initial state (both AA phases) are compared field by
+field with the FP64 oracle run at the same size; a longer 256^3 run is held
+to a property that holds at any size: the cavity, its walls and gravity are
+mirror-symmetric in x, so T, u_y, u_z and S are even in x and u_x is odd
+(FP32 rounding aside: mirrored nodes sum their directions in another order)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_T, TOL_LF = 1e-4, 1e-3
+FULL = {
+    "256^3 Ra 1e6 front at 0.4 H": (256, dict(face=0, Ra=1e6, Pr=0.02, Ste=0.05, Ma=0.1, s0=0.4 * 256, derive=True)),
+    "128^3 Ra 1e5 from s0 = 1": (128, dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)),
+}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1604_03478_gb300 import build, Cavity
+    build.build()
+    return Cavity
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_against_oracle(lib, orc, name):
+    n, kw = FULL[name]
+    gpu = lib(n, n, n, **kw)
+    gpu.step(5)
+    Tg, ug, Sg, lfg = gpu.get()
+    gpu.close()
+    o = orc.Oracle(n, n, n, **kw)
+    o.step(5)
+    To, uo, So, lfo = o.get()
+    del o
+    assert np.abs(Tg - To).max() <= TOL_T
+    assert np.abs(ug - uo).max() <= TOL_T
+    assert np.abs(Sg - So).max() <= 1e-6
+    assert abs(lfg - lfo) <= 1e-6
+
+
+def test_full_size_mirror_symmetry(lib):
+    n, kw = FULL["256^3 Ra 1e6 front at 0.4 H"]
+    gpu = lib(n, n, n, **kw)
+    gpu.step(300)
+    T, u, S, lf = gpu.get()
+    gpu.close()
+    Tm = T[:, :, ::-1]
+    um = u[:, :, ::-1, :]
+    assert np.abs(T - Tm).max() <= 1e-5
+    assert np.abs(u[..., 0] + um[..., 0]).max() <= 1e-6
+    assert np.abs(u[..., 1:] - um[..., 1:]).max() <= 1e-6
+    assert np.abs(S - S[:, ::-1]).max() <= 1e-6
+    assert np.abs(u).max() > 1e-4  # the flow has started
