@@ -59,3 +59,49 @@ def test_full_size_mirror_symmetry(lib):
     assert np.abs(u[..., 1:] - um[..., 1:]).max() <= 1e-6
     assert np.abs(S - S[:, ::-1]).max() <= 1e-6
     assert np.abs(u).max() > 1e-4  # the flow has started
+
+
+def test_full_ensemble_members_match_single_cavities():
+    """The 48-cavity workload of bench.py (71.2 M nodes, sizes 48..160,
+    seeded Ra, Ste and heated face), as autotuned there: every member after
+    10 steps against the same cavity run on its own (FP32 rounding)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1604_03478_gb300 import Cavity, Ensemble, inputs
+    draws = inputs.ensemble(48, 2016)
+    cases = [dict(nx=d["n"], ny=d["n"], nz=d["n"], face=d["face"], Ra=d["Ra"], Pr=0.02, Ste=d["Ste"], Ma=0.1,
+                  s0=0.4 * d["n"], derive=True) for d in draws]
+    ens = Ensemble(cases)
+    ens.set_launch(128, 4, 8)
+    ens.step(10)
+    ens.sync()
+    for k, c in enumerate(cases):
+        single = Cavity(c["nx"], c["ny"], c["nz"], **{kk: v for kk, v in c.items() if kk not in ("nx", "ny", "nz")})
+        single.step(10)
+        a = ens.member(k).get()
+        b = single.get()
+        single.close()
+        assert np.abs(a[0] - b[0]).max() <= 1e-5, k
+        assert np.abs(a[1] - b[1]).max() <= 1e-5, k
+        assert np.abs(a[2] - b[2]).max() <= 1e-6, k
+    ens.close()
+
+
+def test_adjoint_96cube_against_tangent_oracle(lib, orc):
+    """The adjoint workload's cavity (96^3, Ra 1e5, Pr 0.02, Ste 0.1, front
+    from s0 = 1), over 40 steps with sqrt(N) checkpoints: the gradient of the
+    final liquid fraction along Ra and along a seeded wall-field direction
+    against the complex-step tangent-linear oracle, 1e-3 relative."""
+    from paper_1604_03478_gb300 import inputs
+    n, steps = 96, 40
+    kw = dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
+    cav = lib(n, n, n, **kw)
+    cav.set_hot_wall(np.full(cav.ncols, 1.0, np.float32))
+    cav.tape_forward(steps)
+    dth, par = cav.tape_backward(np.full(cav.ncols, 1.0 / (cav.H * cav.ncols)))
+    cav.close()
+    _, _, _, dlf_ra = orc.tangent(n, n, n, steps, dRa=1.0, **kw)
+    assert par["Ra"] == pytest.approx(dlf_ra, rel=1e-3)
+    v = inputs.gaussian_field(n * n, 1.0, 7)
+    _, _, _, dlf_v = orc.tangent(n, n, n, steps, dThw=v, **kw)
+    assert float(dth.ravel() @ v) == pytest.approx(dlf_v, rel=1e-3)
