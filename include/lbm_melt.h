@@ -119,7 +119,13 @@ lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double Pr, doub
                            void *cuda_stream, lbm_melt **out);
 
 /* Advance n >= 0 time steps (Eqs. 1-6 per step: stream-collide, front
-   update, phase flip).  Asynchronous. */
+   update, phase flip).  Asynchronous, with one exception: with Tc == Tm the
+   stream-collide grid stops above the liquid (deep solid nodes have no
+   work), at a height taken from a copy of the running maximum liquid count
+   that the device posts every 4 steps; before a step the host uses the newest
+   copy already complete, else waits for one 16 steps old.  So the host blocks
+   only while it is more than ~16 steps ahead of the device (no effect on the
+   results). */
 lbm_status lbm_melt_step(lbm_melt *h, long long n);
 
 /* Macroscopic outputs, any of them NULL to skip: T per node (solid nodes
@@ -219,7 +225,10 @@ void lbm_melt_destroy(lbm_melt *h);
    dL/d(g beta)} (coef = alpha Ste / (Th - Tm), the Eq. 6 factor; dL/dRa
    chains these through the parameter map of lbm_melt_derive).  Segments are
    recomputed from their checkpoints with one snapshot per step, then
-   reversed; the handle is back in its final state afterwards.  Synchronises. */
+   reversed; the handle is back in its final state afterwards.  Synchronises.
+   Returns LBM_EUNSTABLE (or LBM_ENAN) without computing anything when the
+   front status of the handle is flagged: the reverse sweep relies on fronts
+   that moved at most half a node per step. */
 lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every);
 lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed_dL_dS, double *dL_dTh, double *dL_dparams,
                                   int ptr_kind);
