@@ -117,8 +117,14 @@ __device__ __forceinline__ bool k1_node(const KP &p, const int *jmax, int &x, in
     return x < p.nx && y < p.ny;
 }
 
+// Resident blocks of 128 the stream-collide asks for: 8 (64 registers, a
+// few bytes of spills) for FP16 storage, whose warps move half the bytes and
+// need more of them in flight (+1.3%); none for FP32 (72 registers, 7
+// blocks, no spills; forced to 8 it loses 1%).
+template <typename ST> constexpr int k1_min_blocks() { return sizeof(ST) == 2 ? 8 : 0; }
+
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const int *__restrict__ nb,
                                               const float *__restrict__ gpost, const int *jmax) {
     int x, y, z;
@@ -229,7 +235,7 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
 }
 
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_odd(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
+__global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_odd(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                              const int *__restrict__ js, const int *__restrict__ nb,
                                              const float *__restrict__ gpost, const float *__restrict__ thw_rd,
                                              const float *__restrict__ thw_wr, const __grid_constant__ Links lk,
