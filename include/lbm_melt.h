@@ -135,6 +135,17 @@ lbm_status lbm_melt_step(lbm_melt *h, long long n);
 lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
                         int ptr_kind);
 
+/* The front S and the liquid fraction of the current state (the quantities
+   the paper follows in §3, Figs. 2-4), enqueued on the handle's stream
+   without waiting (either may be NULL): the values land in
+   the caller's buffers when the stream reaches the copies, so they may be
+   read only after lbm_melt_sync (or another synchronising call).  A loop of
+   step + get_async keeps the device busy while earlier results travel; for
+   the copies to overlap, host buffers must be page-locked (pageable ones make
+   the copy wait), and a buffer must not be reused before the copy into it is
+   complete.  Status flags (LBM_EUNSTABLE, LBM_ENAN) surface at the sync. */
+lbm_status lbm_melt_get_async(lbm_melt *h, double *S, double *liquid_fraction, int ptr_kind);
+
 /* Same outputs as lbm_melt_get, without allocating anything.  The paper has
    no counterpart: this serves callers that cannot let a library allocate
    device memory (a time-critical loop in which a cudaMalloc would synchronise

@@ -68,6 +68,7 @@ def load() -> C.CDLL:
         "lbm_melt_step": (C.c_int, [vp, C.c_longlong]),
         "lbm_melt_get": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "lbm_melt_get_noalloc": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+        "lbm_melt_get_async": (C.c_int, [vp, vp, vp, C.c_int]),
         "lbm_melt_get_state": (C.c_int, [vp, vp, vp, vp, C.c_int]),
         "lbm_melt_set_state": (C.c_int, [vp, vp, vp, vp, C.c_int]),
         "lbm_melt_set_hot_wall": (C.c_int, [vp, vp, C.c_int]),

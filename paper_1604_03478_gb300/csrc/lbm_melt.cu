@@ -553,6 +553,21 @@ LBM_API lbm_status lbm_melt_get_report(lbm_melt *h, double *rows, long long max_
     return LBM_OK;
 }
 
+// Liquid fraction = mean front height over H, into dst on the handle's
+// stream: two passes over the columns (chunks of at least 1024 columns per
+// block), then a copy.
+lbm_status enqueue_liquid_fraction(lbm_melt *h, double *dst, int ptr_kind) {
+    const long long nc = h->kp.ncols;
+    const long long nb = std::max<long long>(1, std::min<long long>(kRedBlocks, (nc + 1023) / 1024));
+    const long long chunk = (nc + nb - 1) / nb;
+    k_sum_part<<<(int)nb, 256, 0, h->stream>>>(h->s[h->cur], nc, chunk, h->red_part);
+    k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, 1.0 / ((double)h->kp.H * (double)nc), h->sum_dev);
+    CK(cudaGetLastError(), "sum");
+    CK(cudaMemcpyAsync(dst, h->sum_dev, 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+       "copy lf");
+    return LBM_OK;
+}
+
 LBM_API lbm_status lbm_melt_sync(lbm_melt *h) {
     if (!h) return LBM_EINVAL;
     return check_status(h);
@@ -579,19 +594,21 @@ LBM_API lbm_status lbm_melt_get(lbm_melt *h, float *T, float *u, double *S, doub
     if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               h->stream), "copy S");
     if (liquid_fraction) {
-        // mean front height over H: two passes over the columns, chunks of
-        // at least 1024 columns per block
-        const long long nb = std::max<long long>(1, std::min<long long>(kRedBlocks, ((long long)nc + 1023) / 1024));
-        const long long chunk = ((long long)nc + nb - 1) / nb;
-        k_sum_part<<<(int)nb, 256, 0, h->stream>>>(h->s[h->cur], (long long)nc, chunk, h->red_part);
-        k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, 1.0 / ((double)p.H * (double)nc), h->sum_dev);
-        CK(cudaGetLastError(), "sum");
-        CK(cudaMemcpyAsync(liquid_fraction, h->sum_dev, 8,
-                           ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream), "copy lf");
+        const lbm_status st = enqueue_liquid_fraction(h, liquid_fraction, ptr_kind);
+        if (st != LBM_OK) return st;
     }
     lbm_status st = check_status(h);
     if (!ptr_kind) { cudaFree(Td); cudaFree(ud); }
     return st;
+}
+
+LBM_API lbm_status lbm_melt_get_async(lbm_melt *h, double *S, double *liquid_fraction, int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    if (S)
+        CK(cudaMemcpyAsync(S, h->s[h->cur], (size_t)h->kp.ncols * 8,
+                           ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream), "copy S");
+    if (liquid_fraction) return enqueue_liquid_fraction(h, liquid_fraction, ptr_kind);
+    return LBM_OK;
 }
 
 LBM_API lbm_status lbm_melt_get_state(lbm_melt *h, float *f, float *g, double *S, int ptr_kind) {

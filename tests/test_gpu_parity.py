@@ -229,3 +229,25 @@ def test_totals_and_report(lib, orc):
     np.testing.assert_array_equal(rows[:, 0], [10, 20, 30, 40, 50])
     assert np.all(np.diff(rows[:, 1]) > 0)                                  # melting
     np.testing.assert_array_equal(rows[-1, 1:], [t[k] for k in gpu.TOTAL_KEYS])
+
+
+def test_get_async_matches_get(lib):
+    """lbm_melt_get_async into alternating page-locked buffers, then one
+    sync: the last buffer holds what lbm_melt_get returns for that state."""
+    import ctypes as C
+    import torch
+    from paper_1604_03478_gb300 import _abi
+    L = _abi.load()
+    cav = lib(40, 24, 20, face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
+    S2 = [torch.empty(cav.ncols, dtype=torch.float64).pin_memory() for _ in range(2)]
+    lf2 = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    for t in range(5):
+        cav.step(3)
+        st = L.lbm_melt_get_async(cav._h, C.c_void_p(S2[t & 1].data_ptr()), C.c_void_p(lf2[t & 1].data_ptr()), 0)
+        assert st == 0
+    assert L.lbm_melt_sync(cav._h) == 0
+    _, _, S, lf = cav.get(T=False, u=False)
+    np.testing.assert_array_equal(S2[0].numpy(), S.ravel())
+    assert lf2[0].item() == lf
+    assert not np.array_equal(S2[1].numpy(), S.ravel())  # the state of three steps before
+    cav.close()
