@@ -257,47 +257,64 @@ def _events():
 
 
 def precision_leg(steps=200, twin_steps=400):
-    """FP16-storage throughput at 256^3, and the error of FP32 and FP16
-    storage against the FP64 oracle on a 64^3 twin of the workload."""
+    """The precision study: FP32 and FP16 storage at 256^3 with the heated
+    wall at the side (y = 0, the benchmark workload) and at the bottom
+    (z = 0, Rayleigh-Benard-like), throughput and roofline of each, and the
+    error of each storage against the FP64 oracle on a 64^3 twin."""
     import torch
     import oracle
     from paper_1604_03478_gb300 import Cavity
     stream = torch.cuda.current_stream()
-    out = {}
-    cav = Cavity(N_EDGE, N_EDGE, N_EDGE, precision=1, stream=stream.cuda_stream, **CASE)
-    cav.step(10)
-    cav.sync()
-    cav.set_timing(True)
-    cav.kernel_time(reset=True)
-    e0, e1 = _events()
-    e0.record(stream)
-    cav.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    k1, nk = cav.kernel_time(reset=True)
-    S = cav.get(T=False, u=False)[2]
-    n_liq, n_sol = liquid_counts(S, cav.H)
-    alg = 104.0 * n_liq + 14.0 * n_sol
     peak, _ = hbm_peak()
-    out["fp16_mlups"] = n_liq * steps / (ms * 1e-3) / 1e6
-    out["fp16_roofline"] = {"achieved": alg / (k1 / nk * 1e-3) / 1e9, "frac": alg / (k1 / nk * 1e-3) / 1e9 / peak,
-                            "unit": "GB/s", "bytes_per_liquid_node": 104}
-    cav.close()
-    n = 64
-    case = dict(CASE, s0=0.4 * n)
-    o = oracle.Oracle(n, n, n, **case)
-    o.step(twin_steps)
-    To, uo, So, lfo = o.get()
-    o.close()
-    for prec, name in ((0, "fp32"), (1, "fp16")):
-        c = Cavity(n, n, n, precision=prec, stream=stream.cuda_stream, **case)
-        c.step(twin_steps)
-        Tg, ug, Sg, lfg = c.get()
-        c.close()
-        out["%s_twin_error" % name] = {"max_abs_dT": float(np.abs(Tg - To).max()),
-                                       "max_abs_du": float(np.abs(ug - uo).max()),
-                                       "abs_d_liquid_fraction": abs(lfg - lfo)}
+
+    def throughput(face, prec):
+        cav = Cavity(N_EDGE, N_EDGE, N_EDGE, precision=prec, stream=stream.cuda_stream, **dict(CASE, face=face))
+        cav.step(10)
+        cav.sync()
+        cav.set_timing(True)
+        cav.kernel_time(reset=True)
+        e0, e1 = _events()
+        e0.record(stream)
+        cav.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        k1, nk = cav.kernel_time(reset=True)
+        S = cav.get(T=False, u=False)[2]
+        n_liq, n_sol = liquid_counts(S, cav.H)
+        cav.close()
+        per_liq, per_sol = (208.0, 28.0) if prec == 0 else (104.0, 14.0)
+        alg = per_liq * n_liq + per_sol * n_sol
+        gbs = alg / (k1 / nk * 1e-3) / 1e9
+        return n_liq * steps / (ms * 1e-3) / 1e6, {"achieved": gbs, "frac": gbs / peak, "unit": "GB/s",
+                                                    "bytes_per_liquid_node": per_liq}
+
+    def twin(face):
+        n = 64
+        case = dict(CASE, face=face, s0=0.4 * n)
+        o = oracle.Oracle(n, n, n, **case)
+        o.step(twin_steps)
+        To, uo, So, lfo = o.get()
+        o.close()
+        err = {}
+        for prec, name in ((0, "fp32"), (1, "fp16")):
+            c = Cavity(n, n, n, precision=prec, stream=stream.cuda_stream, **case)
+            c.step(twin_steps)
+            Tg, ug, Sg, lfg = c.get()
+            c.close()
+            err["%s_twin_error" % name] = {"max_abs_dT": float(np.abs(Tg - To).max()),
+                                           "max_abs_du": float(np.abs(ug - uo).max()),
+                                           "abs_d_liquid_fraction": abs(lfg - lfo)}
+        return err
+
+    out = {}
+    out["fp16_mlups"], out["fp16_roofline"] = throughput(0, 1)
+    out.update(twin(0))
+    bottom = {}
+    bottom["fp32_mlups"], bottom["fp32_roofline"] = throughput(1, 0)
+    bottom["fp16_mlups"], bottom["fp16_roofline"] = throughput(1, 1)
+    bottom.update(twin(1))
+    out["bottom_heated"] = bottom
     out["twin"] = "64^3, %d steps from the same initial state, against the FP64 oracle" % twin_steps
     return out
 
