@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the FP16, ensemble and adjoint legs (profiling runs)")
-    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint"],
+    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection"],
                     help="run one of the extra legs alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=0, help="steps of that leg (0: its default)")
     return ap.parse_args()
@@ -319,6 +319,43 @@ def precision_leg(steps=200, twin_steps=400):
     return out
 
 
+def convection_leg(steps=4000, n=128, every=500):
+    """Convection-controlled melting in a 128^3 cavity heated at y = 0 (Ra
+    1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1): liquid and all-node
+    MLUPS over the run, and the liquid fraction against time from the
+    on-device report ring (FP64 totals every `every` steps)."""
+    import torch
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    cav = Cavity(n, n, n, stream=stream.cuda_stream, face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
+    cav.set_report(every, steps // every + 1)
+    cav.set_timing(True)
+    cav.kernel_time(reset=True)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cav.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k1, nk = cav.kernel_time(reset=True)
+    rows = cav.get_report()
+    info = cav.info()
+    cav.close()
+    # liquid node-steps from the recorded liquid counts (trapezoid in time,
+    # starting from one liquid layer)
+    t = np.concatenate([[0.0], rows[:, 0]])
+    nl = np.concatenate([[float(n * n)], rows[:, 4]])
+    liquid_node_steps = float(np.sum(0.5 * (nl[1:] + nl[:-1]) * np.diff(t)))
+    return {"cube": n, "steps": steps, "ms_per_step": ms / steps,
+            "liquid_mlups": liquid_node_steps / (ms * 1e-3) / 1e6,
+            "all_node_mlups": n ** 3 * steps / (ms * 1e-3) / 1e6,
+            "stream_collide_ms_per_launch": k1 / nk,
+            "fourier_number_at_end": info["alpha"] * steps / float(n * n),
+            "liquid_fraction_vs_step": [[int(r[0]), float(r[1])] for r in rows],
+            "workload": "128^3 heated at y=0, Ra 1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1, FP32"}
+
+
 def ensemble_leg(steps=100, n_cav=48, seed=2016):
     """48 seeded cavities of uneven sizes in one persistent launch per run of
     steps, against the same cavities stepped one after another."""
@@ -504,6 +541,7 @@ def run_gpu(args):
         extra["precision"] = precision_leg()
         extra["ensemble"] = ensemble_leg()
         extra["adjoint"] = adjoint_leg()
+        extra["convection"] = convection_leg()
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -540,7 +578,8 @@ def run_gpu(args):
 def run_leg(args):
     import torch
     torch.cuda.set_device(0)
-    legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg}
+    legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg,
+            "convection": convection_leg}
     kw = {"steps": args.leg_steps} if args.leg_steps > 0 else {}
     print(json.dumps({"leg": args.leg, **legs[args.leg](**kw)}))
     return 0
