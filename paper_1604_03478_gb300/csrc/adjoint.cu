@@ -421,14 +421,15 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
         if (in.jn < H) {
             const double sn = in.sn, yg = in.jn + 0.5, lTG = in.lTG;
             if (in.kg < 0) {
-                dthw += -(yg - sn) / sn * lTG;
-                Ls += (Tm - Tw) * (-yg / (sn * sn)) * lTG;
+                const double is = 1.0 / sn;
+                dthw += -(yg - sn) * is * lTG;
+                Ls += (Tm - Tw) * (-yg * is * is) * lTG;
             } else {
-                const double yk = in.kg + 0.5, r = (yg - sn) / (sn - yk);
+                const double yk = in.kg + 0.5, id = 1.0 / (sn - yk), r = (yg - sn) * id;
                 const float lTk = (float)(-r * lTG);
 #pragma unroll
                 for (int i = 0; i < 7; ++i) add[1][i] = lTk;
-                Ls += (Tm - in.Tk) * (-(yg - yk) / ((sn - yk) * (sn - yk))) * lTG;
+                Ls += (Tm - in.Tk) * (-(yg - yk) * id * id) * lTG;
             }
             if (in.jn >= 1) {
                 const float *gL = in.gL, *fL = in.fL, *lgp = in.lgp;
@@ -477,18 +478,23 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
         const double sc = in.sc, sp = in.sp, sq = in.sq;
         const int k = in.k;
         double G, dGds, dGdy0 = 0.0, dGdy1 = 0.0, dGdTw = 0.0;
+        // G exactly as the forward computes it (the clamp test below must
+        // agree with the forward's); the derivatives through reciprocals
         if (k < 0) {
             G = (Tm - Tw) / sc;
-            dGds = -(Tm - Tw) / (sc * sc);
-            dGdTw = -1.0 / sc;
+            const double is = 1.0 / sc;
+            dGds = -(Tm - Tw) * is * is;
+            dGdTw = -is;
         } else {
             const double y1 = in.y1, y0 = in.y0, x1 = k + 0.5;
             const double x0 = k >= 1 ? k - 0.5 : 0.0;
             const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
             G = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
-            dGdy0 = d1 / (h * d0);
-            dGdy1 = -d0 / (h * d1);
-            dGds = (y0 - Tm) / (d0 * d0) + (y1 - Tm) / (d1 * d1);
+            const double ih = k >= 1 ? 1.0 : 2.0;  // h is 1 or 1/2
+            const double i0 = 1.0 / d0, i1 = 1.0 / d1;
+            dGdy0 = d1 * ih * i0;
+            dGdy1 = -d0 * ih * i1;
+            dGds = (y0 - Tm) * i0 * i0 + (y1 - Tm) * i1 * i1;
         }
         const double fac = 1.0 + sp * sp + sq * sq;
         const double v = p.coef * fac * (-G);
