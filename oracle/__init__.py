@@ -285,14 +285,18 @@ class Oracle:
         return dict(zip(INFO_KEYS, v.tolist()))
 
 
-def tangent(nx, ny, nz, steps, dRa=0.0, dThw=None, h=1e-20, **kw):
+def tangent(nx, ny, nz, steps, dRa=0.0, dThw=None, h=1e-20, wall=None, **kw):
     """Directional derivative by complex step: run the oracle in complex
     arithmetic with Ra -> Ra + i h dRa and the heated-wall field -> Th +
     i h dThw (per column), and return (S, dS, lf, dlf): the final front
     heights, the liquid fraction and their derivatives along the direction.
-    The phase flags are those of the unperturbed run (branches on real parts).
+    ``wall`` (per column) replaces the scalar Th as the real part of the
+    heated-wall field before the run.  The phase flags are those of the
+    unperturbed run (branches on real parts).
     """
     o = Oracle(nx, ny, nz, _lib=lib_cs(), **kw)
+    if wall is not None:
+        o.set_hot_wall(wall)
     dT = None if dThw is None else np.ascontiguousarray(np.asarray(dThw, float).reshape(o.ncols) * h)
     st = o._L.orc_cs_perturb(o._h, float(dRa) * h, _p(dT))
     if st != 0:

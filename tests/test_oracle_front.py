@@ -125,3 +125,42 @@ def test_conduction_error_shrinks_under_refinement(orc, Ste):
         errs.append((abs(lf - lf_exact) / lf_exact, dT))
     assert errs[0][0] > errs[1][0] > errs[2][0]
     assert errs[0][1] > errs[1][1] > errs[2][1]
+
+
+def test_receding_front_refreezes_a_node(orc):
+    """Refreezing (R11: flips both ways).  A liquid layer colder than Tm
+    below a flat front makes dT/da > 0 at the front, so Eq. 6 moves it back
+    towards the heated wall; the layer it leaves becomes solid: its f is
+    dropped (reported 0, T reported Tm), and on the next step every link
+    pointing down from it into the liquid bounces back, so the node below
+    receives its own post-collision value in the opposite direction."""
+    n, s0 = 8, 5.51                                   # layer 5 (centre 5.5) just below the front
+    o = orc.Oracle(4, n, 3, face=0, Ra=0, Ste=1.0, Th=1.0, Tm=0.0, s0=s0, s_nu=1.2, s_alpha=1.0)
+    e, w, opp = orc.lattice19()
+    e7, w7, _ = orc.lattice7()
+    nz, ny, nx = o.shape
+    y = (np.arange(ny) + 0.5)[None, :, None] * np.ones(o.shape)
+    # liquid from Th at the wall down to -0.4 just below the front (colder than Tm = 0)
+    T = np.where(y < s0, 1.0 - 1.4 * y / 5.5, 0.0)
+    f0 = np.tile(w[:, None], (1, o.N))
+    o.set_state(f0, w7[:, None] * T.reshape(1, -1), np.full(o.ncols, s0))
+    o.step(1)
+    _, _, s1, _ = o.get()
+    assert np.all(s1 < 5.5) and np.all(s1 > 5.0)    # the front receded over layer 5
+    f1, g1, _ = o.get_state()
+    T1 = o.get()[0]
+    f1 = f1.reshape((19,) + o.shape)
+    assert np.all(f1[:, :, 5, :] == 0.0)              # dropped
+    assert np.all(T1[:, 5, :] == 0.0)                 # reported at Tm
+    # the next step: node (x, 4, z) pulls the directions with e_y = -1 from
+    # layer 5, now solid, so it gets back its own post-collision f_opp(i)
+    S19 = np.array([1.0, 1.19, 1.4, 1.0, 1.2, 1.0, 1.2, 1.0, 1.2, 1.2, 1.4, 1.2, 1.4, 1.2, 1.2, 1.2,
+                    1.98, 1.98, 1.98])
+    x, z = 1, 1
+    fstar, _ = orc.collide_f(f1[:, z, 4, x], S19, [0.0, 0.0, 0.0])
+    o.step(1)
+    f2 = o.get_state()[0].reshape((19,) + o.shape)
+    down = [i for i in range(19) if e[i, 1] == -1]
+    assert len(down) == 5
+    for i in down:
+        assert f2[i, z, 4, x] == pytest.approx(fstar[opp[i]], abs=1e-15)

@@ -145,3 +145,45 @@ def test_tilted_front_moves_along_its_normal(orc, face, axis):
     ds = s1 - s_cols
     inner = ds[:, 1:-1] if axis == "x" else ds[1:-1, :]
     np.testing.assert_allclose(inner, speed, rtol=1e-6)
+
+
+@pytest.mark.parametrize("Th,Tc,Tm", [(3.0, 0.5, 0.5), (3.0, -1.0, 0.5), (1.0, 0.0, 0.0)])
+def test_hydrostatic_rest_state_fixes_buoyancy_scale(orc, Th, Tc, Tm):
+    """The buoyancy scale g beta of the Boussinesq force (section 1, item 4;
+    Eq. 1's F_i) from its definition Ra = g beta (Th - Tm) H^3 / (nu alpha)
+    alone.  A cavity heated from below and entirely liquid (front held at
+    H), far below the onset of Rayleigh-Benard convection (Ra = 10), comes
+    to rest with the linear conduction profile between its isothermal walls;
+    momentum balance then makes the pressure rho c_s^2 (c_s^2 = 1/3) rise
+    from one layer to the next by the force per unit volume between them,
+    rho0 g beta (T - Tm) at the mean temperature of the two layers (exact for
+    a linear profile; the force enters through Guo's half-force shift, so the
+    rest state has sum f e = -F/2).  With Tc < Tm the fluid is colder than
+    Tm above mid-height and the step changes sign there.  Halfway
+    bounce-back of a forced flow at the side walls leaves an odd-even
+    velocity mode of about 1% of the force, so the relation holds to ~1e-5
+    relative, not to round-off."""
+    H, Ra = 8, 10.0
+    o = orc.Oracle(5, 6, H, face=1, Ra=Ra, Pr=1.0, Ste=0.0, Th=Th, Tc=Tc, Tm=Tm, s0=float(H),
+                   s_nu=1.0, s_alpha=1.0)
+    info = o.info()
+    nu, alpha = info["nu"], info["alpha"]
+    # nu and alpha from the relaxation rates (BGK values); alpha is the one
+    # the Neumann and Eq. 7 pins fix
+    assert nu == pytest.approx(1.0 / 6.0, rel=1e-15) and alpha == pytest.approx(0.125, rel=1e-15)
+    gbeta = Ra * nu * alpha / ((Th - Tm) * H ** 3)
+    o.step(4000)
+    T, u, s, lf = o.get()
+    f, g, _ = o.get_state()
+    rho = f.sum(axis=0).reshape(o.shape)
+    zc = np.arange(H) + 0.5
+    np.testing.assert_allclose(T, (Th - (Th - Tc) * zc / H)[:, None, None] * np.ones(o.shape), atol=2e-5)
+    Fmax = gbeta * max(Th - Tm, Tm - Tc)
+    assert np.abs(u).max() < 0.03 * Fmax
+    step = np.diff(rho, axis=0) / 3.0
+    force = gbeta * (0.5 * (T[1:] + T[:-1]) - Tm)
+    np.testing.assert_allclose(step, force, rtol=0, atol=1e-4 * np.abs(force).max())
+    if Tc < Tm:
+        assert step[0].min() > 0 and step[-1].max() < 0
+    else:
+        assert step.min() > 0
