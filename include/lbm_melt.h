@@ -152,12 +152,17 @@ lbm_status lbm_melt_get_async(lbm_melt *h, double *S, double *liquid_fraction, i
    the device, or an application whose own pool allocator owns all device
    memory).  Host-bound results are staged through a fixed array that the
    library holds on every GPU that loads it until the process exits, sized
-   for at most 2097152 nodes (128^3); a larger cavity is rejected with
-   LBM_EINVAL.  The handle's device must be current.  The first call on a
+   for at most 2097152 nodes (128^3, 32 MiB); a larger cavity is rejected
+   with LBM_EINVAL.  The liquid fraction is reduced in the handle's own
+   buffers (allocated at create), so every output equals lbm_melt_get's bit
+   for bit.  The handle's device must be current.  The first call on a
    device performs a one-time set-up (it looks up the array's device
-   address); make that first call before any stream capture.  Every call
-   shares the array: calls whose work overlaps on the GPU race.  Calls no
-   cudaMalloc, cudaFree or allocating library routine.  Synchronises. */
+   address); make that first call before any stream capture.  A device reset
+   (cudaDeviceReset) invalidates that set-up, as it invalidates every handle
+   made before it: do not call this entry point in a process after a reset.
+   Every call shares the array: calls whose work overlaps on the GPU race.
+   Calls no cudaMalloc, cudaFree or allocating library routine.
+   Synchronises. */
 lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
                                 int ptr_kind);
 

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -755,11 +756,17 @@ LBM_API lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *laun
 // that loads the library until the process exits.  All calls share it, so
 // calls whose work overlaps on the GPU race with each other.
 static const long long kNoallocMaxNodes = 2097152;  // 128^3: 16 bytes per node (T and u)
-static __device__ __align__(256) unsigned char g_noalloc_stage[kNoallocMaxNodes * 16 + 256];
+static __device__ __align__(256) unsigned char g_noalloc_stage[kNoallocMaxNodes * 16];
 
 namespace {
 const int kMaxDevices = 64;
-void *g_noalloc_dev[kMaxDevices];  // device address of the array, per device (null: not looked up yet)
+// Device address of the array per device, looked up once (with that device
+// current) under a once-flag, so that concurrent first calls from several
+// host threads do the set-up once.  A reset of the device (cudaDeviceReset)
+// invalidates the address, as it does every handle made before it.
+void *g_noalloc_dev[kMaxDevices];
+cudaError_t g_noalloc_err[kMaxDevices];
+std::once_flag g_noalloc_once[kMaxDevices];
 }  // namespace
 
 LBM_API lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double *S, double *liquid_fraction,
@@ -774,17 +781,17 @@ LBM_API lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double 
     CK(cudaGetDevice(&dev), "get device");
     if (dev != h->device || dev < 0 || dev >= kMaxDevices)
         return set_err(h, LBM_EINVAL, "make the handle's device (%d) current before lbm_melt_get_noalloc", h->device);
-    if (!g_noalloc_dev[dev]) {
-        // one-time set-up on this device (the device is current): the host-side
-        // name of the array is only a stand-in, so look up its device address
+    // one-time set-up on this device (the device is current): the host-side
+    // name of the array is only a stand-in, so look up its device address
+    std::call_once(g_noalloc_once[dev], [dev]() {
         void *ptr = nullptr;
-        CK(cudaGetSymbolAddress(&ptr, g_noalloc_stage), "staging array address");
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_stage);
         g_noalloc_dev[dev] = ptr;
-    }
+    });
+    CK(g_noalloc_err[dev], "staging array address");
     unsigned char *stage = (unsigned char *)g_noalloc_dev[dev];
     float *Td = ptr_kind ? T : (float *)stage;
     float *ud = ptr_kind ? u : (float *)(stage + N * 4);
-    double *lfd = ptr_kind ? liquid_fraction : (double *)(stage + kNoallocMaxNodes * 16);
     if (T || u) {
         Bufs b = bufs(h);
         CK(LAUNCH(h, macro, p, h->face, h->inflight, b, T ? Td : nullptr, u ? ud : nullptr, h->stream), "macro");
@@ -796,9 +803,10 @@ LBM_API lbm_status lbm_melt_get_noalloc(lbm_melt *h, float *T, float *u, double 
     if (S) CK(cudaMemcpyAsync(S, h->s[h->cur], nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               h->stream), "copy S");
     if (liquid_fraction) {
-        k_sum<<<1, 1024, 0, h->stream>>>(h->s[h->cur], (long long)nc, 1.0 / ((double)p.H * (double)nc), lfd);
-        CK(cudaGetLastError(), "sum");
-        if (!ptr_kind) CK(cudaMemcpyAsync(liquid_fraction, lfd, 8, cudaMemcpyDeviceToHost, h->stream), "copy lf");
+        // the handle's own reduction buffers, allocated at create: the same
+        // two-pass sum as lbm_melt_get
+        const lbm_status st = enqueue_liquid_fraction(h, liquid_fraction, ptr_kind);
+        if (st != LBM_OK) return st;
     }
     return check_status(h);
 }

@@ -5,7 +5,8 @@ loop in which a cudaMalloc would synchronise the device, or an application
 whose pool allocator owns all device memory.  For them lbm_melt_get_noalloc
 stages host-bound results through a fixed array instead of per-call
 buffers.  This checks it through the C ABI against lbm_melt_get on two calls
-in a row, and that a cavity beyond its stated maximum is rejected.  The file
+in a row (bit for bit: both run the same kernels on the same state), and
+that a cavity beyond its stated maximum is rejected.  The file
 is named to be collected last.
 """
 import ctypes as C
@@ -15,7 +16,6 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TOL_T, TOL_LF = 1e-4, 1e-3
 
 
 def _get(L, h, shape, ncols, fn):
@@ -40,10 +40,11 @@ def test_get_noalloc_matches_get_on_two_calls():
         cav.step(steps)  # the second call also sees values in flight (odd total)
         ref = _get(L, cav._h, cav.shape, cav.ncols, L.lbm_melt_get)
         out = _get(L, cav._h, cav.shape, cav.ncols, L.lbm_melt_get_noalloc)
-        np.testing.assert_allclose(out[0], ref[0], atol=TOL_T, rtol=0)
-        np.testing.assert_allclose(out[1], ref[1], atol=TOL_T, rtol=0)
-        np.testing.assert_allclose(out[2], ref[2], atol=TOL_LF, rtol=0)
-        assert abs(out[3] - ref[3]) <= TOL_LF
+        # the same kernels on the same state in the same order: bit for bit
+        np.testing.assert_array_equal(out[0], ref[0])
+        np.testing.assert_array_equal(out[1], ref[1])
+        np.testing.assert_array_equal(out[2], ref[2])
+        assert out[3] == ref[3]
     cav.close()
 
 
