@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection"],
                     help="run one of the extra legs alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=0, help="steps of that leg (0: its default)")
+    ap.add_argument("--dump-dir", default=None, help="directory for the convection leg's final front map (.npy)")
     return ap.parse_args()
 
 
@@ -204,21 +205,34 @@ def liquid_counts(S, H):
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_sample(steps, warm=0, n=N_EDGE):
+def oracle_sample(steps, warm=0, n=N_EDGE, single_steps=0):
     """Time the FP64 oracle on the workload (edge n, same parameters, front
-    at 0.4 n) on this host's cores."""
+    at 0.4 n) on this host's cores; with single_steps > 0, then time that
+    many more steps on one thread.  Returns (MLUPS, seconds, threads) and,
+    for the single-thread sample, (MLUPS, seconds) or None."""
     import oracle
     oracle.build()
     case = dict(CASE, s0=0.4 * n)
     o = oracle.Oracle(n, n, n, **case)
+    threads = oracle.num_threads()
     if warm:
         o.step(warm)
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     n_liq = o.info()["n_liquid"]  # after the steps; the front moves < 1 cell
+    single = None
+    if single_steps > 0:
+        oracle.set_num_threads(1)
+        t0 = time.perf_counter()
+        o.step(single_steps)
+        dt1 = time.perf_counter() - t0
+        oracle.set_num_threads(threads)
+        single = (n_liq * single_steps / dt1 / 1e6, dt1)
     o.close()
-    return n_liq * steps / dt / 1e6, dt, oracle.num_threads()
+    if single_steps > 0:
+        return n_liq * steps / dt / 1e6, dt, threads, single
+    return n_liq * steps / dt / 1e6, dt, threads
 
 
 def run_reference(args):
@@ -319,40 +333,69 @@ def precision_leg(steps=200, twin_steps=400):
     return out
 
 
-def convection_leg(steps=4000, n=128, every=500):
+def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
     """Convection-controlled melting in a 128^3 cavity heated at y = 0 (Ra
-    1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1): liquid and all-node
-    MLUPS over the run, and the liquid fraction against time from the
-    on-device report ring (FP64 totals every `every` steps)."""
+    1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1), the whole 20000-step
+    run: liquid and all-node MLUPS, the stream-collide's HBM roofline
+    fraction over the run (algorithmic bytes of the liquid and active solid
+    nodes of each step over the summed stream-collide time), the liquid
+    fraction against time from the on-device report ring (FP64 totals every
+    `every` steps) and a summary of the final front S(x, z).  The run goes
+    in chunks of `every` steps with the front read back between them (for
+    the node counts); only the chunks are timed."""
     import torch
     from paper_1604_03478_gb300 import Cavity
     stream = torch.cuda.current_stream()
+    peak, _ = hbm_peak()
     cav = Cavity(n, n, n, stream=stream.cuda_stream, face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
     cav.set_report(every, steps // every + 1)
     cav.set_timing(True)
     cav.kernel_time(reset=True)
-    e0, e1 = _events()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    cav.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    S = cav.get(T=False, u=False)[2]
+    counts = [liquid_counts(S, cav.H)]
+    ms = 0.0
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cav.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        done += k
+        S = cav.get(T=False, u=False)[2]
+        counts.append(liquid_counts(S, cav.H))
     k1, nk = cav.kernel_time(reset=True)
     rows = cav.get_report()
     info = cav.info()
     cav.close()
-    # liquid node-steps from the recorded liquid counts (trapezoid in time,
-    # starting from one liquid layer)
-    t = np.concatenate([[0.0], rows[:, 0]])
-    nl = np.concatenate([[float(n * n)], rows[:, 4]])
-    liquid_node_steps = float(np.sum(0.5 * (nl[1:] + nl[:-1]) * np.diff(t)))
+    # node-steps by the trapezoid rule over the chunks (counts change by at
+    # most one node per column and step)
+    c = np.asarray(counts, dtype=np.float64)
+    w = np.diff(np.concatenate([[0], np.minimum(np.arange(1, len(c)) * every, steps)]))
+    liq_steps = float(np.sum(0.5 * (c[1:, 0] + c[:-1, 0]) * w))
+    sol_steps = float(np.sum(0.5 * (c[1:, 1] + c[:-1, 1]) * w))
+    alg = 208.0 * liq_steps + 28.0 * sol_steps
+    gbs = alg / (k1 * 1e-3) / 1e9
+    mid = n // 2
+    if dump_dir:
+        os.makedirs(dump_dir, exist_ok=True)
+        np.save(os.path.join(dump_dir, "convection_128cube_front.npy"), S)
     return {"cube": n, "steps": steps, "ms_per_step": ms / steps,
-            "liquid_mlups": liquid_node_steps / (ms * 1e-3) / 1e6,
+            "liquid_mlups": liq_steps / (ms * 1e-3) / 1e6,
             "all_node_mlups": n ** 3 * steps / (ms * 1e-3) / 1e6,
             "stream_collide_ms_per_launch": k1 / nk,
-            "fourier_number_at_end": info["alpha"] * steps / float(n * n),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "kernel": "fused stream-collide, averaged over the run",
+                         "algorithmic_bytes": alg, "stream_collide_ms": k1},
+            "stream_collide_share_of_step": k1 / ms,
+            "fourier_number_at_end": info["alpha"] * (info["t0"] + steps) / float(n * n),
             "liquid_fraction_vs_step": [[int(r[0]), float(r[1])] for r in rows],
+            "front": {"mean": float(S.mean()), "min": float(S.min()), "max": float(S.max()),
+                      "at_mid_x_vs_z": [[int(z), float(S[z, mid])] for z in range(0, n, 8)] + [[n - 1, float(S[n - 1, mid])]],
+                      "layout": "S[z, x], heights above the heated wall y = 0 in lattice units"},
             "workload": "128^3 heated at y=0, Ra 1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1, FP32"}
 
 
@@ -532,16 +575,18 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, cores = oracle_sample(2, n=n)
+        v, dt, cores, (v1, dt1) = oracle_sample(2, n=n, single_steps=1)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "2 oracle steps of the full %d^3 workload from its initial state (%.1f s)" % (n, dt)}
+               "sample": "2 oracle steps of the full %d^3 workload from its initial state (%.1f s)" % (n, dt),
+               "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
+                                 "sample": "1 more oracle step of the same run on one thread (%.1f s)" % dt1}}
 
     extra = {}
     if rank == 0 and world == 1 and not args.skip_extra and n == N_EDGE and args.precision == 0:
         extra["precision"] = precision_leg()
         extra["ensemble"] = ensemble_leg()
         extra["adjoint"] = adjoint_leg()
-        extra["convection"] = convection_leg()
+        extra["convection"] = convection_leg(dump_dir=args.dump_dir)
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -581,6 +626,8 @@ def run_leg(args):
     legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg,
             "convection": convection_leg}
     kw = {"steps": args.leg_steps} if args.leg_steps > 0 else {}
+    if args.leg == "convection":
+        kw["dump_dir"] = args.dump_dir
     print(json.dumps({"leg": args.leg, **legs[args.leg](**kw)}))
     return 0
 

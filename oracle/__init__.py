@@ -73,10 +73,12 @@ def _declare(L):
     L.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp]
     L.orc_set_state.argtypes = [C.c_void_p, dp, dp, dp]
     L.orc_set_hot_wall.argtypes = [C.c_void_p, dp]
+    L.orc_nusselt.argtypes = [C.c_void_p, dp, dp]
     L.orc_info.argtypes = [C.c_void_p, dp]
     L.orc_error.restype = C.c_char_p
     L.orc_error.argtypes = [C.c_void_p]
     L.orc_num_threads.restype = C.c_int
+    L.orc_set_num_threads.argtypes = [C.c_int]
 
 
 def lib_cs() -> C.CDLL:
@@ -200,6 +202,11 @@ def num_threads():
     return lib().orc_num_threads()
 
 
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loops from now on (timing only)."""
+    lib().orc_set_num_threads(int(n))
+
+
 # ---------------------------------------------------------------- simulator
 
 INFO_KEYS = ("nu", "alpha", "gbeta", "lambda", "t0", "s_nu", "s_alpha", "H", "steps",
@@ -278,6 +285,14 @@ class Oracle:
     def set_hot_wall(self, Thw):
         Thw = np.ascontiguousarray(Thw, float).reshape(self.ncols)
         self._L.orc_set_hot_wall(self._h, _p(Thw))
+
+    def nusselt(self):
+        """Local Nusselt number on the heated wall per column (cols_shape)
+        and its mean over the wall, from the last step's wall flux."""
+        nu = np.zeros(self.ncols)
+        m = np.zeros(1)
+        self._L.orc_nusselt(self._h, _p(nu), _p(m))
+        return nu.reshape(self.cols_shape), float(m[0])
 
     def info(self):
         v = np.zeros(len(INFO_KEYS))

@@ -771,6 +771,29 @@ void orc_get(const orc_sim *S, double *T, double *u, double *s, double *lf) {
     }
 }
 
+/* Local Nusselt number on the heated wall (the heat-surface diagnostic of
+   section 3.2, Fig. 4(b)): Nu = -H (dT/da at the wall) / (Th - Tm), the
+   conduction flux through the wall expressed against the scalar Th.  The
+   flux is the heat the last step's streaming carried through each wall link
+   of the column, incoming population minus the outgoing post-collision one
+   (in - out on the anti-bounce-back link of the first node), and equals
+   -alpha dT/da there.  Per column (column order of S) and the mean over the
+   wall.  Defined after at least one step. */
+void orc_nusselt(const orc_sim *S, double *Nu, double *Nu_mean) {
+    int up = S->cfg.face == 0 ? 3 : 5; /* the D3Q7 direction pointing away from the heated wall */
+    int down = opp7(up);
+    double scale = (double)S->H / (RE(S->alpha) * (S->cfg.Th - S->cfg.Tm));
+    double acc = 0.0;
+    for (long col = 0; col < S->ncols; ++col) {
+        long c = column_cell(S, col, 0);
+        double q = RE(S->g[c * Q7 + up]) - RE(S->gs[c * Q7 + down]);
+        double nu = q * scale;
+        if (Nu) Nu[col] = nu;
+        acc += nu;
+    }
+    if (Nu_mean) *Nu_mean = acc / (double)S->ncols;
+}
+
 /* Natural (post-streaming, pre-collision) distributions, direction major. */
 void orc_get_state(const orc_sim *S, double *f, double *g, double *s) {
     if (f)
@@ -832,6 +855,16 @@ int orc_num_threads(void) {
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Threads of the OpenMP loops from now on (a timing knob; no effect on the
+   results, which do not depend on the thread count). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }
 
