@@ -370,6 +370,7 @@ def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
     k1, nk = cav.kernel_time(reset=True)
     rows = cav.get_report()
     info = cav.info()
+    nu, nu_mean = cav.nusselt()
     cav.close()
     # node-steps by the trapezoid rule over the chunks (counts change by at
     # most one node per column and step)
@@ -383,6 +384,7 @@ def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
     if dump_dir:
         os.makedirs(dump_dir, exist_ok=True)
         np.save(os.path.join(dump_dir, "convection_128cube_front.npy"), S)
+        np.save(os.path.join(dump_dir, "convection_128cube_nusselt.npy"), nu)
     return {"cube": n, "steps": steps, "ms_per_step": ms / steps,
             "liquid_mlups": liq_steps / (ms * 1e-3) / 1e6,
             "all_node_mlups": n ** 3 * steps / (ms * 1e-3) / 1e6,
@@ -393,6 +395,10 @@ def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
             "stream_collide_share_of_step": k1 / ms,
             "fourier_number_at_end": info["alpha"] * (info["t0"] + steps) / float(n * n),
             "liquid_fraction_vs_step": [[int(r[0]), float(r[1])] for r in rows],
+            "nusselt_mean_vs_step": [[int(r[0]), float(r[7])] for r in rows],
+            "nusselt": {"mean": nu_mean, "at_mid_x_vs_z": [[int(z), float(nu[z, mid])] for z in range(0, n, 16)],
+                        "mean_over_z_vs_x": [[int(x), float(nu[:, x].mean())] for x in range(0, n, 16)],
+                        "layout": "Nu[z, x] on the heated wall y = 0, -H dT/dy / (Th - Tm)"},
             "front": {"mean": float(S.mean()), "min": float(S.min()), "max": float(S.max()),
                       "at_mid_x_vs_z": [[int(z), float(S[z, mid])] for z in range(0, n, 8)] + [[n - 1, float(S[n - 1, mid])]],
                       "layout": "S[z, x], heights above the heated wall y = 0 in lattice units"},

@@ -187,16 +187,30 @@ lbm_status lbm_melt_set_state(lbm_melt *h, const float *f, const float *g, const
 lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, int ptr_kind);
 
 /* FP64 totals of the current state (paper §3.1 and Fig. 4(d): the liquid
-   fraction; energy and mass balances): out[0] liquid fraction, out[1]
-   sum over liquid nodes of (T - Tm), out[2] sum over liquid nodes of
-   (rho - 1), out[3] number of liquid nodes, out[4] max |u| over liquid nodes,
-   out[5] sum of S over columns.  The heat content relative to solid at Tm is
+   fraction; energy and mass balances; §3.2, Fig. 4(b): the heat-surface
+   Nusselt number): out[0] liquid fraction, out[1] sum over liquid nodes of
+   (T - Tm), out[2] sum over liquid nodes of (rho - 1), out[3] number of
+   liquid nodes, out[4] max |u| over liquid nodes, out[5] sum of S over
+   columns, out[6] mean Nusselt number over the heated wall (as
+   lbm_melt_get_nusselt).  The heat content relative to solid at Tm is
    out[1] + (Th - Tm) / Ste * out[5].  Deterministic (fixed reduction order).
    Synchronises. */
 lbm_status lbm_melt_totals(lbm_melt *h, double *out, int ptr_kind);
 
+/* Heat-surface Nusselt number (paper §3.2, Fig. 4(b) and the Case 1 / Case
+   2 comparison of Fig. 5): Nu = -H (dT/da at the heated wall) / (Th - Tm)
+   per column, from the heat that the last step's streaming carried through
+   the heated-wall link of the column's first node (incoming minus outgoing
+   population on that anti-bounce-back link, which equals -alpha dT/da),
+   with the wall field of that streaming and the scalar Th.  Nu: ncols
+   doubles in the column order of S (NULL: not wanted); Nu_mean: one double,
+   the mean over the wall by a fixed-order FP64 sum (NULL: not wanted).
+   Meaningful after at least one step (after create or set_state it is
+   computed from the uploaded populations).  Synchronises. */
+lbm_status lbm_melt_get_nusselt(lbm_melt *h, double *Nu, double *Nu_mean, int ptr_kind);
+
 /* Record the totals every `every` steps (0 turns recording off) into a ring
-   of `capacity` rows of 7 doubles {steps, out[0..5] of lbm_melt_totals},
+   of `capacity` rows of 8 doubles {steps, out[0..6] of lbm_melt_totals},
    filled on the device inside lbm_melt_step.  Clears earlier rows. */
 lbm_status lbm_melt_set_report(lbm_melt *h, long long every, long long capacity);
 

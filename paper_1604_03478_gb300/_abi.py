@@ -75,6 +75,7 @@ def load() -> C.CDLL:
         "lbm_melt_get_info": (C.c_int, [vp, C.POINTER(lbm_melt_info)]),
         "lbm_melt_sync": (C.c_int, [vp]),
         "lbm_melt_totals": (C.c_int, [vp, vp, C.c_int]),
+        "lbm_melt_get_nusselt": (C.c_int, [vp, vp, vp, C.c_int]),
         "lbm_melt_set_report": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
         "lbm_melt_get_report": (C.c_int, [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]),
         "lbm_melt_set_timing": (C.c_int, [vp, C.c_int]),

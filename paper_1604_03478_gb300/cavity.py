@@ -122,22 +122,31 @@ class Cavity:
         self._check(_abi.load().lbm_melt_get(self._h, _ptr(Ta), _ptr(ua), _ptr(Sa), _ptr(la), 0))
         return Ta, ua, Sa, (float(la[0]) if lf else None)
 
-    TOTAL_KEYS = ("liquid_fraction", "sum_T_minus_Tm", "sum_rho_minus_1", "n_liquid", "max_u", "sum_S")
+    TOTAL_KEYS = ("liquid_fraction", "sum_T_minus_Tm", "sum_rho_minus_1", "n_liquid", "max_u", "sum_S",
+                  "nusselt_mean")
 
     def totals(self):
         """FP64 totals of the current state (see lbm_melt_totals)."""
-        out = np.zeros(6, np.float64)
+        out = np.zeros(len(self.TOTAL_KEYS), np.float64)
         self._check(_abi.load().lbm_melt_totals(self._h, _ptr(out), 0))
         return dict(zip(self.TOTAL_KEYS, out.tolist()))
+
+    def nusselt(self):
+        """Heat-surface Nusselt number per column (cols_shape) and its mean
+        over the heated wall (see lbm_melt_get_nusselt)."""
+        nu = np.zeros(self.cols_shape, np.float64)
+        m = np.zeros(1, np.float64)
+        self._check(_abi.load().lbm_melt_get_nusselt(self._h, _ptr(nu), _ptr(m), 0))
+        return nu, float(m[0])
 
     def set_report(self, every, capacity=4096):
         self._check(_abi.load().lbm_melt_set_report(self._h, int(every), int(capacity)))
 
     def get_report(self, max_rows=1 << 20):
-        """Recorded rows: columns steps, then the six totals."""
+        """Recorded rows: columns steps, then the seven totals."""
         n = C.c_longlong()
         self._check(_abi.load().lbm_melt_get_report(self._h, None, 0, C.byref(n)))
-        rows = np.zeros((min(n.value, max_rows), 7), np.float64)
+        rows = np.zeros((min(n.value, max_rows), 8), np.float64)
         self._check(_abi.load().lbm_melt_get_report(self._h, _ptr(rows), rows.shape[0], C.byref(n)))
         return rows
 

@@ -183,7 +183,7 @@ void advance_handles(lbm_ensemble *e, long long n) {
     for (lbm_melt *h : e->cav) {
         h->steps += n;
         if (n & 1) { h->cur ^= 1; h->inflight ^= 1; }
-        if (n > 0) h->thw_pending = 0;
+        if (n > 0) { h->thw_pending = 0; h->thw_last_prev = 0; }
         h->exec_steps += n;  // the launch kept the running maximum: host read-backs stay bounds
     }
     e->steps += n;

@@ -33,12 +33,15 @@ struct lbm_melt {
     float *gpost;
     float *thw_cur, *thw_prev;
     int thw_pending;   // set_hot_wall happened while values were in flight
+    int thw_last_prev; // set_hot_wall since the last step in the natural layout: thw_prev holds the
+                       // field of the last streaming (the Nusselt number's wall value)
+    double *nu_dev;    // per-column Nusselt numbers (ncols)
     int *status_dev;
     double *sum_dev;
     double *red_part;  // scratch: per-block partials of the FP64 totals
     int nred;          // number of partial blocks
-    double *totals_dev;  // 6 doubles
-    double *report;    // ring of report rows (7 doubles: t, totals)
+    double *totals_dev;  // 7 doubles
+    double *report;    // ring of report rows (8 doubles: t, totals)
     long long report_every, report_cap, report_rows;
     int inflight;      // last stream-collide was an even (local) step
     long long steps;

@@ -681,6 +681,30 @@ __global__ void __launch_bounds__(128) k_init(const __grid_constant__ KP p, ST *
     for (int i = 0; i < 7; ++i) Store<ST>::st(G + i * p.ld + c, w7(i) * dT);
 }
 
+// ---------------------------------------------------------- Nusselt number
+// Heat-surface Nusselt number per column (section 3.2, Fig. 4(b)):
+// Nu = -H (dT/da at the heated wall) / (Th - Tm), from the heat the last
+// streaming carried through the wall link of the column's first node,
+// q = in - out = -alpha dT/da, times scale = H / (alpha (Th - Tm)).  The
+// link is anti-bounce-back, in = -out + 2 w (Tw - Tm) in shifted values, so
+// slot +a of the node gives q alone: in the natural layout it holds `in`
+// (q = 2 (in - w (Tw - Tm))); in flight it still holds `out`, the node's
+// post-collision population towards the wall (q = 2 (w (Tw - Tm) - out)).
+// Tw is the wall field of that streaming.  FP64 from the stored value.
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_nusselt(const __grid_constant__ KP p, const ST *__restrict__ G,
+                                                 const float *__restrict__ thw, int inflight, double scale,
+                                                 double *__restrict__ nu) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p.ncols) return;
+    int x, y, z;
+    column_node<FACE>(p, col, 0, x, y, z);
+    constexpr int up = FACE == 0 ? 3 : 5;  // the D3Q7 direction leaving the heated wall
+    const double v = (double)Store<ST>::ld(G + up * p.ld + node_index(p, x, y, z));
+    const double wt = (double)w7(up) * ((double)thw[col] - p.Tm_d);
+    nu[col] = (inflight ? 2.0 * (wt - v) : 2.0 * (v - wt)) * scale;
+}
+
 // ------------------------------------------------------ FP64 reductions
 // Block partials of the liquid-node totals: sum (T - Tm), sum (rho - 1),
 // count, max |u|^2.  Fixed block and thread order: deterministic.
@@ -724,21 +748,26 @@ __global__ void __launch_bounds__(256) k_totals_part(const __grid_constant__ KP 
 }
 
 // Final pass in one block: out = {liquid fraction, sum (T - Tm), sum (rho - 1),
-// liquid nodes, max |u|, sum s}; with t >= 0 also writes the time first.
+// liquid nodes, max |u|, sum s, mean Nusselt number over the heated wall
+// (of the per-column values nu)}; with t >= 0 also writes the time first.
 static __global__ void __launch_bounds__(256) k_totals_final(const double *__restrict__ part, int nparts,
-                                                      const double *__restrict__ s, int ncols, double H,
+                                                      const double *__restrict__ s,
+                                                      const double *__restrict__ nu, int ncols, double H,
                                                       double t, double *__restrict__ out) {
-    __shared__ double sh[5][256];
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, ss = 0.0;
+    __shared__ double sh[6][256];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, ss = 0.0, sn = 0.0;
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
         a0 += part[b * 4];
         a1 += part[b * 4 + 1];
         a2 += part[b * 4 + 2];
         a3 = fmax(a3, part[b * 4 + 3]);
     }
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) ss += s[c];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        ss += s[c];
+        sn += nu[c];
+    }
     sh[0][threadIdx.x] = a0; sh[1][threadIdx.x] = a1; sh[2][threadIdx.x] = a2; sh[3][threadIdx.x] = a3;
-    sh[4][threadIdx.x] = ss;
+    sh[4][threadIdx.x] = ss; sh[5][threadIdx.x] = sn;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) {
@@ -747,6 +776,7 @@ static __global__ void __launch_bounds__(256) k_totals_final(const double *__res
             sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
             sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
             sh[4][threadIdx.x] += sh[4][threadIdx.x + w];
+            sh[5][threadIdx.x] += sh[5][threadIdx.x + w];
         }
         __syncthreads();
     }
@@ -759,6 +789,7 @@ static __global__ void __launch_bounds__(256) k_totals_final(const double *__res
         o[3] = sh[2][0];
         o[4] = sqrt(sh[3][0]);
         o[5] = sh[4][0];
+        o[6] = sh[5][0] / (double)ncols;
     }
 }
 

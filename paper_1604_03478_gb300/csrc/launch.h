@@ -23,6 +23,9 @@ struct Bufs {
     int cblk;                    // threads per block of the per-column kernels (col_block)
     int *jmax;                   // running maximum of the liquid counts (k_front), or null
     int k1_height;               // the stream-collide grid covers heights < k1_height (the rest is deep solid)
+    const float *thw_nu;         // heated-wall field of the last streaming (Nusselt number)
+    double *nu;                  // per-column Nusselt numbers (ncols)
+    double nu_scale;             // H / (alpha (Th - Tm))
 };
 
 template <typename ST> struct Launch {
@@ -35,6 +38,7 @@ template <typename ST> struct Launch {
     static cudaError_t init(const KP &p, int face, const Bufs &b, const float *Tprof, cudaStream_t st);
     static cudaError_t totals(const KP &p, int face, int inflight, const Bufs &b, double *part, int nparts,
                               double t, double *out, cudaStream_t st);
+    static cudaError_t nusselt(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st);
 };
 
 // Threads per block of the per-column kernels (front, flip and their

@@ -84,7 +84,18 @@ cudaError_t Launch<ST>::totals(const KP &p, int face, int inflight, const Bufs &
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0) k_totals_part<ST, 0><<<nparts, 256, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, part);
     else k_totals_part<ST, 1><<<nparts, 256, 0, st>>>(p, F, G, b.js, b.thw_rd, inflight, part);
-    k_totals_final<<<1, 256, 0, st>>>(part, nparts, b.s, p.ncols, (double)p.H, t, out);
+    const cudaError_t e = nusselt(p, face, inflight, b, st);
+    if (e != cudaSuccess) return e;
+    k_totals_final<<<1, 256, 0, st>>>(part, nparts, b.s, b.nu, p.ncols, (double)p.H, t, out);
+    return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t Launch<ST>::nusselt(const KP &p, int face, int inflight, const Bufs &b, cudaStream_t st) {
+    const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
+    const ST *G = (const ST *)b.G;
+    if (face == 0) k_nusselt<ST, 0><<<grd, blk, 0, st>>>(p, G, b.thw_nu, inflight, b.nu_scale, b.nu);
+    else k_nusselt<ST, 1><<<grd, blk, 0, st>>>(p, G, b.thw_nu, inflight, b.nu_scale, b.nu);
     return cudaGetLastError();
 }
 

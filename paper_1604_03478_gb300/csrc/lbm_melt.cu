@@ -156,6 +156,12 @@ Bufs bufs(lbm_melt *h) {
     b.cblk = h->cblk;
     b.jmax = h->jmax_dev;
     b.k1_height = h->kp.H;
+    // the wall field of the last streaming: in flight, the one the pending
+    // reads will apply; in the natural layout, the one the last odd step
+    // wrote with, unless a new field has been set since
+    b.thw_nu = h->inflight ? b.thw_rd : (h->thw_last_prev ? h->thw_prev : h->thw_cur);
+    b.nu = h->nu_dev;
+    b.nu_scale = (double)h->kp.H / (h->d.alpha * (h->Th - h->Tm));
     return b;
 }
 
@@ -199,6 +205,7 @@ void free_all(lbm_melt *h) {
     cudaFree(h->sum_dev);
     cudaFree(h->red_part);
     cudaFree(h->totals_dev);
+    cudaFree(h->nu_dev);
     cudaFree(h->report);
     cudaFree(h->jmax_dev);
     if (h->rb_val) cudaFreeHost(h->rb_val);
@@ -399,8 +406,8 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         {(void **)&h->nb[0], nc * 4}, {(void **)&h->nb[1], nc * 4},
         {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
         {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
-        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 6 * 8},
-        {(void **)&h->jmax_dev, sizeof(int)}};
+        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 7 * 8},
+        {(void **)&h->jmax_dev, sizeof(int)}, {(void **)&h->nu_dev, nc * 8}};
     h->nred = kRedBlocks;
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.b);
@@ -491,6 +498,7 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         if (evp) CK(cudaEventRecord(evp[1], h->stream), "event record");
         h->inflight = !odd;
         if (odd) h->thw_pending = 0;
+        h->thw_last_prev = 0;
         b = bufs(h);
         CK(LAUNCH(h, front, h->kp, h->face, h->inflight, 1, b, h->stream), "front");
         CK(LAUNCH(h, flip, h->kp, h->face, h->inflight, 1, b, h->stream), "flip");
@@ -499,7 +507,7 @@ LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
         h->exec_steps++;
         if ((hs = jmax_readback(h)) != LBM_OK) return hs;
         if (h->report_every > 0 && h->steps % h->report_every == 0) {
-            double *row = h->report + 7 * (h->report_rows % h->report_cap);
+            double *row = h->report + 8 * (h->report_rows % h->report_cap);
             b = bufs(h);
             CK(LAUNCH(h, totals, h->kp, h->face, h->inflight, b, h->red_part, h->nred, (double)h->steps, row,
                       h->stream), "report totals");
@@ -514,7 +522,7 @@ LBM_API lbm_status lbm_melt_totals(lbm_melt *h, double *out, int ptr_kind) {
     Bufs b = bufs(h);
     CK(LAUNCH(h, totals, h->kp, h->face, h->inflight, b, h->red_part, h->nred, -1.0, h->totals_dev, h->stream),
        "totals");
-    CK(cudaMemcpyAsync(out, h->totals_dev, 6 * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(out, h->totals_dev, 7 * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        h->stream), "copy totals");
     return check_status(h);
 }
@@ -528,7 +536,7 @@ LBM_API lbm_status lbm_melt_set_report(lbm_melt *h, long long every, long long c
     h->report_cap = 0;
     h->report_rows = 0;
     if (every == 0) return LBM_OK;
-    CK(cudaMalloc(&h->report, (size_t)capacity * 7 * 8), "alloc report");
+    CK(cudaMalloc(&h->report, (size_t)capacity * 8 * 8), "alloc report");
     h->report_every = every;
     h->report_cap = capacity;
     return LBM_OK;
@@ -549,24 +557,29 @@ LBM_API lbm_status lbm_melt_get_report(lbm_melt *h, double *rows, long long max_
     const long long first = h->report_rows - avail;
     for (long long r = 0; r < n; ++r) {
         const long long slot = (first + r) % h->report_cap;
-        CK(cudaMemcpy(rows + 7 * r, h->report + 7 * slot, 7 * 8, cudaMemcpyDeviceToHost), "copy report");
+        CK(cudaMemcpy(rows + 8 * r, h->report + 8 * slot, 8 * 8, cudaMemcpyDeviceToHost), "copy report");
     }
     return LBM_OK;
 }
 
-// Liquid fraction = mean front height over H, into dst on the handle's
+// scale * (sum of the ncols column values v), into dst on the handle's
 // stream: two passes over the columns (chunks of at least 1024 columns per
-// block), then a copy.
-lbm_status enqueue_liquid_fraction(lbm_melt *h, double *dst, int ptr_kind) {
+// block, fixed order), then a copy.
+lbm_status enqueue_column_sum(lbm_melt *h, const double *v, double scale, double *dst, int ptr_kind) {
     const long long nc = h->kp.ncols;
     const long long nb = std::max<long long>(1, std::min<long long>(kRedBlocks, (nc + 1023) / 1024));
     const long long chunk = (nc + nb - 1) / nb;
-    k_sum_part<<<(int)nb, 256, 0, h->stream>>>(h->s[h->cur], nc, chunk, h->red_part);
-    k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, 1.0 / ((double)h->kp.H * (double)nc), h->sum_dev);
+    k_sum_part<<<(int)nb, 256, 0, h->stream>>>(v, nc, chunk, h->red_part);
+    k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, scale, h->sum_dev);
     CK(cudaGetLastError(), "sum");
     CK(cudaMemcpyAsync(dst, h->sum_dev, 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
-       "copy lf");
+       "copy sum");
     return LBM_OK;
+}
+
+// Liquid fraction = mean front height over H (Σ s / (H ncols)).
+lbm_status enqueue_liquid_fraction(lbm_melt *h, double *dst, int ptr_kind) {
+    return enqueue_column_sum(h, h->s[h->cur], 1.0 / ((double)h->kp.H * (double)h->kp.ncols), dst, ptr_kind);
 }
 
 LBM_API lbm_status lbm_melt_sync(lbm_melt *h) {
@@ -690,8 +703,29 @@ LBM_API lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, in
         // the step that produced the in-flight values
         CK(cudaMemcpyAsync(h->thw_prev, h->thw_cur, nc * 4, cudaMemcpyDeviceToDevice, h->stream), "copy wall");
         h->thw_pending = 1;
+    } else if (!h->inflight && !h->thw_last_prev) {
+        // keep the field of the last streaming for the Nusselt number until
+        // the next step (the next step, an even one, reads no wall)
+        CK(cudaMemcpyAsync(h->thw_prev, h->thw_cur, nc * 4, cudaMemcpyDeviceToDevice, h->stream), "copy wall");
+        h->thw_last_prev = 1;
     }
     return copy_in(h, h->thw_cur, T_h_field, nc * 4, ptr_kind);
+}
+
+LBM_API lbm_status lbm_melt_get_nusselt(lbm_melt *h, double *Nu, double *Nu_mean, int ptr_kind) {
+    if (!h) return LBM_EINVAL;
+    if (Nu || Nu_mean) {
+        Bufs b = bufs(h);
+        CK(LAUNCH(h, nusselt, h->kp, h->face, h->inflight, b, h->stream), "nusselt");
+        if (Nu)
+            CK(cudaMemcpyAsync(Nu, h->nu_dev, (size_t)h->kp.ncols * 8,
+                               ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream), "copy Nu");
+        if (Nu_mean) {
+            const lbm_status st = enqueue_column_sum(h, h->nu_dev, 1.0 / (double)h->kp.ncols, Nu_mean, ptr_kind);
+            if (st != LBM_OK) return st;
+        }
+    }
+    return check_status(h);
 }
 
 LBM_API lbm_status lbm_melt_get_info(lbm_melt *h, lbm_melt_info *info) {

@@ -12,6 +12,9 @@ pytestmark = pytest.mark.gpu
 W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 W7 = np.array([1 / 4] + [1 / 8] * 6)
 TOL_T, TOL_LF = 1e-4, 1e-3
+# Nusselt numbers: H / alpha times a difference of FP32 populations near the
+# wall, relative to the largest value
+TOL_NU = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -225,6 +228,7 @@ def test_totals_and_report(lib, orc):
     assert abs(t["sum_rho_minus_1"] - (i["mass"] - nl)) <= 1e-5 * nl
     assert abs(t["max_u"] - np.sqrt((uo ** 2).sum(-1)).max()) <= 1e-4
     assert abs(t["sum_S"] - So.sum()) <= TOL_LF * So.size
+    assert abs(t["nusselt_mean"] - o.nusselt()[1]) <= TOL_NU * abs(t["nusselt_mean"])
     rows = gpu.get_report()
     np.testing.assert_array_equal(rows[:, 0], [10, 20, 30, 40, 50])
     assert np.all(np.diff(rows[:, 1]) > 0)                                  # melting
@@ -251,3 +255,37 @@ def test_get_async_matches_get(lib):
     assert lf2[0].item() == lf
     assert not np.array_equal(S2[1].numpy(), S.ravel())  # the state of three steps before
     cav.close()
+
+
+@pytest.mark.parametrize("face,shape", [(0, (20, 16, 12)), (1, (18, 12, 16))])
+@pytest.mark.parametrize("steps", [30, 31])
+def test_nusselt_against_oracle(lib, orc, face, shape, steps):
+    """Heat-surface Nusselt number per column (section 3.2, Fig. 4(b)) under
+    a seeded heated-wall field, after an even and an odd step count (values
+    in flight or streamed); a field set afterwards changes the next
+    streaming, not the Nusselt number of the last one."""
+    kw = dict(face=face, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
+    gpu, o = _pair(lib, orc, shape, **kw)
+    wall = (1.0 + inputs.gaussian_field(o.ncols, 0.05, 17)).astype(np.float32)
+    gpu.set_hot_wall(wall)
+    o.set_hot_wall(wall.astype(np.float64))
+    gpu.step(steps)
+    o.step(steps)
+    nu_g, m_g = gpu.nusselt()
+    nu_o, m_o = o.nusselt()
+    scale = np.abs(nu_o).max()
+    assert scale > 1.0
+    np.testing.assert_allclose(nu_g, nu_o, rtol=0, atol=TOL_NU * scale)
+    assert abs(m_g - m_o) <= TOL_NU * scale
+    assert gpu.totals()["nusselt_mean"] == pytest.approx(m_g, rel=1e-12)  # another summation order
+    wall2 = (1.0 + inputs.gaussian_field(o.ncols, 0.05, 18)).astype(np.float32)
+    gpu.set_hot_wall(wall2)
+    o.set_hot_wall(wall2.astype(np.float64))
+    nu_g2, m_g2 = gpu.nusselt()
+    np.testing.assert_array_equal(nu_g2, nu_g)
+    assert m_g2 == m_g
+    gpu.step(1)
+    o.step(1)
+    nu_g, m_g = gpu.nusselt()
+    nu_o, m_o = o.nusselt()
+    np.testing.assert_allclose(nu_g, nu_o, rtol=0, atol=TOL_NU * scale)
