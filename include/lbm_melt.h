@@ -236,6 +236,18 @@ lbm_status lbm_melt_set_launch(lbm_melt *h, int bx, int by);
 lbm_status lbm_melt_set_timing(lbm_melt *h, int enable);
 lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, int reset);
 
+/* Replay lbm_melt_step's steps from CUDA graphs of `steps` steps each (0:
+   launch every step on its own).  A step is three kernels; on a small
+   cavity the host's launches take longer than the GPU's work, so by default
+   cavities of at most 160^3 nodes replay 16 steps per graph and larger ones
+   launch step by step.  A graph is captured once per starting phase of the
+   in-place streaming (and again when the front outgrows the grid it was
+   captured for) and replayed on the handle's stream; results are
+   bit-identical to step-by-step launches.  Steps that carry a report row,
+   follow a heated-wall change still pending, or are timed
+   (lbm_melt_set_timing) run step by step.  steps in [0, 256]. */
+lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps);
+
 const char *lbm_melt_last_error(const lbm_melt *h);
 void lbm_melt_destroy(lbm_melt *h);
 

@@ -203,6 +203,10 @@ class Cavity:
     def set_timing(self, on=True):
         self._check(_abi.load().lbm_melt_set_timing(self._h, 1 if on else 0))
 
+    def set_graph_steps(self, steps):
+        """Steps per CUDA-graph replay in step() (0: step by step)."""
+        self._check(_abi.load().lbm_melt_set_graph_steps(self._h, int(steps)))
+
     def kernel_time(self, reset=True):
         ms = C.c_double()
         n = C.c_longlong()

@@ -69,6 +69,16 @@ struct lbm_melt {
     double Ra;         // as given to create
     int derived_from_Ra;
     void *tape;        // recorded run for the adjoint (adjoint.cu)
+    // Steps replayed from CUDA graphs (lbm_melt_step): graph_steps steps per
+    // replay (0: every step launched on its own).  One instantiated graph per
+    // starting (cur, inflight) phase; each records the stream-collide grid
+    // height and block shape it was captured with.
+    int graph_steps;
+    cudaStream_t cap_stream;     // private stream the graphs are captured on
+    struct StepGraph {
+        cudaGraphExec_t exec;
+        int height, bx, by;
+    } graphs[2][2];              // [cur][inflight]
     std::vector<cudaEvent_t> ev;  // start/stop pairs of timed launches
     size_t ev_used;
     char err[512];

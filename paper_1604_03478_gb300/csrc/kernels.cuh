@@ -316,16 +316,17 @@ __device__ __forceinline__ void gather_f9(const KP &p, const ST *F, const int (&
     }
 }
 
-// Tm + the sum of the shifted g, in FP64 (the temperature the front reads).
-__device__ __forceinline__ double sum_T(const KP &p, const float (&g)[7]) {
-    double t = 0.0;
+// Tm + the sum of the shifted g (the temperature the front reads; FP32, the
+// precision the populations are held in).
+__device__ __forceinline__ float sum_T(const KP &p, const float (&g)[7]) {
+    float t = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) t += (double)g[i];
-    return p.Tm_d + t;
+    for (int i = 0; i < 7; ++i) t += g[i];
+    return p.Tm + t;
 }
 
 template <typename ST, int FACE>
-__device__ __forceinline__ double node_T(const KP &p, const ST *G, int col, int j, bool inflight, const float *thw) {
+__device__ __forceinline__ float node_T(const KP &p, const ST *G, int col, int j, bool inflight, const float *thw) {
     int x, y, z;
     column_node<FACE>(p, col, j, x, y, z);
     float g[7];
@@ -349,6 +350,13 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // move = 0 keeps the front (used to prepare the ghost after a state upload).
 // SPEC: load the ghost's likely source node together with the gradient
 // stencil (two dependent load stages instead of three; more registers).
+//
+// Precision: the front heights are accumulated in FP64 (s + ds, and the
+// distances from s to the stencil nodes and the ghost are FP64 differences);
+// the gradient, the speed and the ghost temperature are FP32 arithmetic, the
+// precision of the temperatures they are made of.  GB300 issues FP64 at a
+// small fraction of its FP32 rate, and the FP64 divisions of an all-FP64
+// version made this kernel FP64-pipe bound.
 template <typename ST, int FACE, bool SPEC = true>
 __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
                                            const int *__restrict__ js, int *__restrict__ js_next,
@@ -360,21 +368,21 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     const bool infl = inflight != 0;
     // Load stage 1: what depends on the column only.
     const double sc = s[col];
-    const double Tm = p.Tm_d;
-    const double Tw = (double)thw[col];
+    const float Tm = p.Tm;
+    const float Tw = thw[col];
     const int jsc = js[col];
     int js9[9];
     if (SPEC && infl) load_js9(p, js, pp, q, js9);
-    double sp = 0.0, sq = 0.0;
+    float sp = 0.0f, sq = 0.0f;
     if (move) {
-        sp = 0.5 * (s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
-        sq = 0.5 * (s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
+        sp = 0.5f * (float)(s[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s[q * P1 + (pp > 0 ? pp - 1 : pp)]);
+        sq = 0.5f * (float)(s[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s[(q > 0 ? q - 1 : q) * P1 + pp]);
     }
     // Load stage 2: the gradient stencil of s_t and, speculatively, the node
     // below the current front, which is the ghost's source node whenever the
     // liquid count does not change (all but a few columns per step).
     const int k = move ? guarded_node(sc, H) : -2;
-    double y1 = 0.0, y0 = Tw;
+    float y1 = 0.0f, y0 = Tw;
     if (k >= 0) {
         y1 = node_T<ST, FACE>(p, G, col, k, infl, thw);
         if (k >= 1) y0 = node_T<ST, FACE>(p, G, col, k - 1, infl, thw);
@@ -392,22 +400,22 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     // Then Eq. 6.
     double sn = sc;
     if (move) {
-        double Gr;
+        float Gr;
         if (k < 0) {
-            Gr = (Tm - Tw) / sc;
+            Gr = (Tm - Tw) / (float)sc;
         } else {
             // derivative at x2 = s of the quadratic through (x0, y0), (x1, y1),
             // (x2, Tm): with h = x1 - x0, d1 = x2 - x1, d0 = x2 - x0,
             // p'(x2) = (y0 d1^2 - y1 d0^2 + Tm h (d0 + d1)) / (h d0 d1)
             const double x1 = k + 0.5;
             const double x0 = k >= 1 ? k - 0.5 : 0.0;
-            const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
+            const float h = (float)(x1 - x0), d1 = (float)(sc - x1), d0 = (float)(sc - x0);
             Gr = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
         }
-        const double v = p.coef * (1.0 + sp * sp + sq * sq) * (-Gr);
+        const float v = p.coef_f * (1.0f + sp * sp + sq * sq) * (-Gr);
         if (!isfinite(Gr)) atomicOr(status, 2);
-        else if (!(fabs(v) <= 0.5)) atomicOr(status, 1);
-        sn = sc + v;
+        else if (!(fabsf(v) <= 0.5f)) atomicOr(status, 1);
+        sn = sc + (double)v;
         if (!(sn >= 0.5)) sn = 0.5;  // also catches NaN
         if (sn > (double)H) sn = (double)H;
     }
@@ -418,22 +426,22 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     if (jn >= H) return jn;  // fully liquid column: no ghost node
     const double yg = jn + 0.5;
     const int kg = guarded_node(sn, H);
-    double Tg;
+    float Tg;
     if (kg < 0) {
-        Tg = Tm + (Tm - Tw) * (yg - sn) / sn;
+        Tg = Tm + (Tm - Tw) * ((float)(yg - sn) / (float)sn);
     } else {
-        double Tk;
+        float Tk;
         if (kg == k) Tk = y1;
         else if (kg == k - 1 && k >= 1) Tk = y0;
         else if (spec && kg == L) Tk = sum_T(p, gL);
         else Tk = node_T<ST, FACE>(p, G, col, kg, infl, thw);
-        Tg = Tm + (Tm - Tk) * (yg - sn) / (sn - (kg + 0.5));
+        Tg = Tm + (Tm - Tk) * ((float)(yg - sn) / (float)(sn - (kg + 0.5)));
     }
     // ghost populations (FP32, like the collision): rest equilibrium at the
     // ghost temperature plus the non-equilibrium part N^-1 (I - Q)(n - n^eq)
     // of the post-collision populations of the liquid node below
     float gh[7];
-    const float dTg = (float)(Tg - Tm);
+    const float dTg = Tg - Tm;
 #pragma unroll
     for (int i = 0; i < 7; ++i) gh[i] = w7(i) * dTg;
     if (jn >= 1) {

@@ -109,6 +109,7 @@ struct KP {
     float s_alpha, s_g4, s_g5;
     double Tm_d, Th_d;
     double coef;      // alpha Ste / (Th - Tm): Eq. 6 front speed per unit -dT/da
+    float coef_f;     // the same in FP32 (the front speed is FP32 arithmetic)
     int skip_deep;    // Tc == Tm: deep solid nodes need no update
 };
 

@@ -27,6 +27,11 @@ namespace {
 
 const double CS2T = 0.25;  // D3Q7 pseudo sound speed squared (w0 = 1/4)
 const int kRedBlocks = 608;  // partial blocks of the FP64 totals (4 per SM of a GB300)
+// Step graphs: steps per replay, and the largest cavity that uses them by
+// default (a 160^3 step takes about as long on the GPU as its three launches
+// take the host; larger cavities are bound by the GPU).
+const int kGraphSteps = 16;
+const long long kGraphMaxNodes = 160LL * 160 * 160;
 
 
 
@@ -138,16 +143,17 @@ lbm_status cuda_err(lbm_melt *h, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_err(h, e_, where); \
     } while (0)
 
-Bufs bufs(lbm_melt *h) {
+// Buffers of a step from phase (cur, inflight) with the handle's wall fields.
+Bufs bufs_at(lbm_melt *h, int cur, int inflight) {
     Bufs b;
     b.F = h->F;
     b.G = h->G;
-    b.js = h->js[h->cur];
-    b.js_next = h->js[1 - h->cur];
-    b.nb = h->nb[h->cur];
-    b.nb_next = h->nb[1 - h->cur];
-    b.s = h->s[h->cur];
-    b.s_next = h->s[1 - h->cur];
+    b.js = h->js[cur];
+    b.js_next = h->js[1 - cur];
+    b.nb = h->nb[cur];
+    b.nb_next = h->nb[1 - cur];
+    b.s = h->s[cur];
+    b.s_next = h->s[1 - cur];
     b.gpost = h->gpost;
     b.thw_rd = h->thw_pending ? h->thw_prev : h->thw_cur;
     b.thw_wr = h->thw_cur;
@@ -159,11 +165,13 @@ Bufs bufs(lbm_melt *h) {
     // the wall field of the last streaming: in flight, the one the pending
     // reads will apply; in the natural layout, the one the last odd step
     // wrote with, unless a new field has been set since
-    b.thw_nu = h->inflight ? b.thw_rd : (h->thw_last_prev ? h->thw_prev : h->thw_cur);
+    b.thw_nu = inflight ? b.thw_rd : (h->thw_last_prev ? h->thw_prev : h->thw_cur);
     b.nu = h->nu_dev;
     b.nu_scale = (double)h->kp.H / (h->d.alpha * (h->Th - h->Tm));
     return b;
 }
+
+Bufs bufs(lbm_melt *h) { return bufs_at(h, h->cur, h->inflight); }
 
 #define LAUNCH(h, method, ...)                                                       \
     ((h)->precision == 1 ? lbm::Launch<__half>::method(__VA_ARGS__)                  \
@@ -213,6 +221,11 @@ void free_all(lbm_melt *h) {
         if (h->rb_ev[k]) cudaEventDestroy(h->rb_ev[k]);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
+    for (auto &row : h->graphs)
+        for (auto &g : row)
+            if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
 }
 
 // Height bound of the next stream-collide grid (see lbm_melt::kRbLag): all
@@ -253,9 +266,10 @@ lbm_status seed_readback(lbm_melt *h) {
     return LBM_OK;
 }
 
-// After every kRbEvery-th step: copy the running maximum into the next ring slot.
-lbm_status jmax_readback(lbm_melt *h) {
-    if (!h->kp.skip_deep || h->exec_steps % lbm_melt::kRbEvery) return LBM_OK;
+// After every kRbEvery-th step (or now, with force): copy the running
+// maximum into the next ring slot.
+lbm_status jmax_readback(lbm_melt *h, bool force = false) {
+    if (!h->kp.skip_deep || (!force && h->exec_steps % lbm_melt::kRbEvery)) return LBM_OK;
     const int slot = (int)(h->rb_next % lbm_melt::kRbRing);
     CK(cudaMemcpyAsync(h->rb_val + slot, h->jmax_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read-back");
     CK(cudaEventRecord(h->rb_ev[slot], h->stream), "read-back event");
@@ -302,6 +316,79 @@ __global__ void k_fill_f(float *p, long long n, float v) {
 __global__ void k_fill_d(double *p, long long n, double v) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
+}
+
+// Launch shape of the stream-collide.
+dim3 sc_block(const lbm_melt *h) { return h->bx ? dim3(h->bx, h->by, 1) : lbm::node_block(h->kp); }
+
+// Enqueue one step from phase (cur, inflight) on stream st with the
+// stream-collide grid cut at `height`; returns the phase after it.
+cudaError_t enqueue_step(lbm_melt *h, int &cur, int &inflight, int height, dim3 blk, cudaStream_t st) {
+    Bufs b = bufs_at(h, cur, inflight);
+    b.k1_height = height;
+    const int odd = inflight;
+    cudaError_t e = LAUNCH(h, stream_collide, h->kp, h->face, odd, b, blk, st);
+    if (e != cudaSuccess) return e;
+    inflight = !odd;
+    b = bufs_at(h, cur, inflight);
+    e = LAUNCH(h, front, h->kp, h->face, inflight, 1, b, st);
+    if (e == cudaSuccess) e = LAUNCH(h, flip, h->kp, h->face, inflight, 1, b, st);
+    cur ^= 1;
+    return e;
+}
+
+// The graph of graph_steps steps from the handle's phase with the
+// stream-collide grid cut at `height` or higher: the cached one when it was
+// captured for this phase and block shape at a height from `height` to
+// height + 32, else a new capture (heights rounded up to a multiple of 8).
+// The replays are bit-identical to single steps: the extra blocks of a
+// higher grid find only deep solid nodes and return at once.
+lbm_status step_graph(lbm_melt *h, int height, cudaGraphExec_t *out) {
+    const dim3 blk = sc_block(h);
+    lbm_melt::StepGraph &g = h->graphs[h->cur][h->inflight];
+    if (g.exec && g.bx == (int)blk.x && g.by == (int)blk.y && g.height >= height && g.height <= height + 32) {
+        *out = g.exec;
+        return LBM_OK;
+    }
+    const int H = h->kp.H;
+    int hc = std::min(H, (height + 7) / 8 * 8);
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int cur = h->cur, inflight = h->inflight;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k) e = enqueue_step(h, cur, inflight, hc, blk, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && g.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    }
+    if (e == cudaSuccess && !g.exec) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_err(h, e, "step graph");
+    }
+    g.height = hc;
+    g.bx = (int)blk.x;
+    g.by = (int)blk.y;
+    *out = g.exec;
+    return LBM_OK;
+}
+
+// Whether the next graph_steps steps may be replayed from a graph: no timed
+// launches, no wall field pending (the graphs read the walls of thw_cur), no
+// report row due within them.
+bool graph_eligible(const lbm_melt *h, long long left) {
+    const long long G = h->graph_steps;
+    if (G <= 0 || left < G || h->timing || h->thw_pending) return false;
+    if (h->report_every > 0 && (h->steps + G) / h->report_every != h->steps / h->report_every) return false;
+    return true;
 }
 
 }  // namespace
@@ -371,6 +458,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     p.s_alpha = (float)d.s_alpha; p.s_g4 = (float)d.s_g4; p.s_g5 = (float)d.s_g5;
     p.Tm_d = Tm; p.Th_d = Th;
     p.coef = Ste > 0.0 ? d.alpha * Ste / (Th - Tm) : 0.0;
+    p.coef_f = (float)p.coef;
     p.skip_deep = (Tc == Tm) ? 1 : 0;
     {
         const long long sy = p.nx, sz = (long long)p.nx * p.ny;
@@ -395,6 +483,8 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         h->sms = sms;
     }
     h->rb_synced = -1;
+    // small cavities are launch bound: replay their steps from graphs
+    h->graph_steps = d.N <= kGraphMaxNodes ? kGraphSteps : 0;
     if (cudaMallocHost(&h->rb_val, lbm_melt::kRbRing * sizeof(int)) != cudaSuccess) return fail(LBM_ENOMEM);
     for (int k = 0; k < lbm_melt::kRbRing; ++k)
         if (cudaEventCreateWithFlags(&h->rb_ev[k], cudaEventDisableTiming) != cudaSuccess) return fail(LBM_ECUDA);
@@ -475,8 +565,26 @@ LBM_API const char *lbm_melt_last_error(const lbm_melt *h) { return h ? h->err :
 LBM_API lbm_status lbm_melt_step(lbm_melt *h, long long n) {
     if (!h) return LBM_EINVAL;
     if (n < 0) return set_err(h, LBM_EINVAL, "negative step count");
-    const dim3 blk = h->bx ? dim3(h->bx, h->by, 1) : lbm::node_block(h->kp);
+    const dim3 blk = sc_block(h);
     for (long long t = 0; t < n; ++t) {
+        if (graph_eligible(h, n - t)) {
+            // graph_steps steps in one replay; the grid height bound of the
+            // first of them grows by one node per step over the replay
+            int height = 0;
+            lbm_status hs = k1_height(h, &height);
+            if (hs != LBM_OK) return hs;
+            cudaGraphExec_t exec = nullptr;
+            if ((hs = step_graph(h, std::min(h->kp.H, height + h->graph_steps), &exec)) != LBM_OK) return hs;
+            CK(cudaGraphLaunch(exec, h->stream), "step graph launch");
+            const int G = h->graph_steps;
+            if (G & 1) { h->cur ^= 1; h->inflight ^= 1; }
+            h->thw_last_prev = 0;
+            h->steps += G;
+            h->exec_steps += G;
+            if ((hs = jmax_readback(h, true)) != LBM_OK) return hs;
+            t += G - 1;
+            continue;
+        }
         Bufs b = bufs(h);
         lbm_status hs = k1_height(h, &b.k1_height);
         if (hs != LBM_OK) return hs;
@@ -755,6 +863,19 @@ LBM_API lbm_status lbm_melt_set_launch(lbm_melt *h, int bx, int by) {
         return set_err(h, LBM_EINVAL, "block shape must be a multiple of 32 along x with at most 128 threads");
     h->bx = bx;
     h->by = by;
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps) {
+    if (!h) return LBM_EINVAL;
+    if (steps < 0 || steps > 256) return set_err(h, LBM_EINVAL, "graph steps must be in [0, 256]");
+    if (steps != h->graph_steps) {
+        CK(cudaStreamSynchronize(h->stream), "synchronize");
+        for (auto &row : h->graphs)
+            for (auto &g : row)
+                if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+        h->graph_steps = steps;
+    }
     return LBM_OK;
 }
 
