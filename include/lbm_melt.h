@@ -270,7 +270,10 @@ void lbm_melt_destroy(lbm_melt *h);
    reversed; the handle is back in its final state afterwards.  Synchronises.
    Returns LBM_EUNSTABLE (or LBM_ENAN) without computing anything when the
    front status of the handle is flagged: the reverse sweep relies on fronts
-   that moved at most half a node per step. */
+   that moved at most half a node per step; and LBM_EINVAL when the
+   heated-wall field was set after the recorded run (the sweep recomputes
+   the run with it).  The recomputed segments of full length are captured
+   into CUDA graphs once and replayed. */
 lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every);
 lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed_dL_dS, double *dL_dTh, double *dL_dparams,
                                   int ptr_kind);

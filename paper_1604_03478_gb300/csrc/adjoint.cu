@@ -180,14 +180,16 @@ __device__ __forceinline__ void collide_adjoint(const KP &p, const float (&f)[19
 }
 
 // Temperature of node j of column col in a snapshot; cn receives its index.
+// Summed in FP32 in the order of the forward's front update (the snapshot
+// holds the values it read), so the recomputed gradient is the forward's.
 template <int FACE>
-__device__ __forceinline__ double snap_T(const KP &p, const float *snap, int col, int j, long long &cn) {
+__device__ __forceinline__ float snap_T(const KP &p, const float *snap, int col, int j, long long &cn) {
     int x, y, z;
     column_node<FACE>(p, col, j, x, y, z);
     cn = node_index(p, x, y, z);
-    double t = 0.0;
-    for (int i = 0; i < 7; ++i) t += (double)snap[(19 + i) * p.N + cn];
-    return p.Tm_d + t;
+    float t = 0.0f;
+    for (int i = 0; i < 7; ++i) t += snap[(19 + i) * p.N + cn];
+    return p.Tm + t;
 }
 
 // The slopes s_p, s_q of column c' read the fronts of its neighbours (with a
@@ -330,14 +332,16 @@ __global__ void __launch_bounds__(128) k_adj_node(const __grid_constant__ KP p, 
 struct ColIn {
     // ghost
     int jn, kg;
-    double sn, slope, lTG;
+    double sn, slope;
+    float lTG;
     float lgp[7];
     long long ck, cL;
-    double Tk;
+    float Tk;
     float fL[19], gL[7];
     // front
     int k;
-    double sc, sp, sq, y0, y1;
+    double sc;
+    float sp, sq, y0, y1;
     long long c1, c0;
 };
 
@@ -353,7 +357,9 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                                            double *__restrict__ wp_prev, double *__restrict__ wq_prev) {
     const int H = p.H, P1 = p.P1, P2 = p.P2;
     const long long N = p.N;
-    const double Tm = p.Tm_d, Tw = (double)thw[col];
+    // FP32 arithmetic as in the forward front update; the adjoint of the
+    // front (lambda_s) and the parameter and wall sums accumulate in FP64
+    const float Tm = p.Tm, Tw = thw[col];
     const int pp = col % P1, q = col / P1;
     ColIn in;
     in.jn = H;
@@ -367,11 +373,11 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
         in.slope = slope_terms(p, wp, wq, col);
         in.jn = js[col];
         in.sn = s[col];
-        in.lTG = 0.0;
+        in.lTG = 0.0f;
 #pragma unroll
         for (int i = 0; i < 7; ++i) {
             in.lgp[i] = lgpost[(long long)i * p.ncols + col];
-            in.lTG += (double)w7(i) * in.lgp[i];
+            in.lTG = __fmaf_rn(w7(i), in.lgp[i], in.lTG);
         }
         if (in.jn < H) {
             in.kg = guarded_node(in.sn, H);
@@ -389,8 +395,8 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     }
     if (FRONT) {
         in.sc = s_prev[col];
-        in.sp = 0.5 * (s_prev[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s_prev[q * P1 + (pp > 0 ? pp - 1 : pp)]);
-        in.sq = 0.5 * (s_prev[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s_prev[(q > 0 ? q - 1 : q) * P1 + pp]);
+        in.sp = 0.5f * (float)(s_prev[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s_prev[q * P1 + (pp > 0 ? pp - 1 : pp)]);
+        in.sq = 0.5f * (float)(s_prev[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s_prev[(q > 0 ? q - 1 : q) * P1 + pp]);
         in.k = guarded_node(in.sc, H);
         in.y0 = Tw;
         if (in.k >= 0) {
@@ -419,17 +425,20 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     if (GHOST) {
         Ls += in.slope;
         if (in.jn < H) {
-            const double sn = in.sn, yg = in.jn + 0.5, lTG = in.lTG;
+            const double sn = in.sn, yg = in.jn + 0.5;
+            const float lTG = in.lTG, dy = (float)(yg - sn);
             if (in.kg < 0) {
-                const double is = 1.0 / sn;
-                dthw += -(yg - sn) * is * lTG;
-                Ls += (Tm - Tw) * (-yg * is * is) * lTG;
+                const float is = __fdiv_rn(1.0f, (float)sn);
+                dthw += (double)(-__fmul_rn(__fmul_rn(dy, is), lTG));
+                Ls += (double)__fmul_rn(__fmul_rn(__fsub_rn(Tm, Tw), __fmul_rn(__fmul_rn(-(float)yg, is), is)), lTG);
             } else {
-                const double yk = in.kg + 0.5, id = 1.0 / (sn - yk), r = (yg - sn) * id;
-                const float lTk = (float)(-r * lTG);
+                const double yk = in.kg + 0.5;
+                const float id = __fdiv_rn(1.0f, (float)(sn - yk)), r = __fmul_rn(dy, id);
+                const float lTk = -__fmul_rn(r, lTG);
 #pragma unroll
                 for (int i = 0; i < 7; ++i) add[1][i] = lTk;
-                Ls += (Tm - in.Tk) * (-(yg - yk) * id * id) * lTG;
+                Ls += (double)__fmul_rn(__fmul_rn(__fsub_rn(Tm, in.Tk), __fmul_rn(__fmul_rn(-(float)(yg - yk), id), id)),
+                                        lTG);
             }
             if (in.jn >= 1) {
                 const float *gL = in.gL, *fL = in.fL, *lgp = in.lgp;
@@ -446,9 +455,13 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                 const float Nl4 = 6.0f * lgp[0] - (lgp[1] + lgp[2] + lgp[3] + lgp[4] + lgp[5] + lgp[6]);
                 const float Nl5 = 2.0f * (lgp[1] + lgp[2]) - (lgp[3] + lgp[4] + lgp[5] + lgp[6]);
                 const float Nl6 = (lgp[3] + lgp[4]) - (lgp[5] + lgp[6]);
-                const float d1 = (gL[1] - gL[2]) - ux * TL, d2 = (gL[3] - gL[4]) - uy * TL,
-                            d3 = (gL[5] - gL[6]) - uz * TL;
-                lsal[col] += -(double)(i1 * (Nl1 * d1 + Nl2 * d2 + Nl3 * d3));
+                // rounded one by one (no contraction): the kernels running this
+                // part (with and without the front part) agree bit for bit
+                const float d1 = __fsub_rn(gL[1] - gL[2], __fmul_rn(ux, TL));
+                const float d2 = __fsub_rn(gL[3] - gL[4], __fmul_rn(uy, TL));
+                const float d3 = __fsub_rn(gL[5] - gL[6], __fmul_rn(uz, TL));
+                lsal[col] += -(double)__fmul_rn(
+                    i1, __fadd_rn(__fadd_rn(__fmul_rn(Nl1, d1), __fmul_rn(Nl2, d2)), __fmul_rn(Nl3, d3)));
                 const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
                 float mu[7];
                 mu[0] = 0.0f;
@@ -459,8 +472,11 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                 mu[5] = r5 * i5 * Nl5;
                 mu[6] = r5 * i6 * Nl6;
                 const float lux = -mu[1] * TL, luy = -mu[2] * TL, luz = -mu[3] * TL;
-                const float lTh = -(mu[1] * ux + mu[2] * uy + mu[3] * uz) - 0.75f * mu[4] + 0.5f * p.gbeta * luz;
-                lgb[col] += 0.5 * (double)Th * (double)luz;
+                const float lTh = __fadd_rn(
+                    __fsub_rn(-__fadd_rn(__fadd_rn(__fmul_rn(mu[1], ux), __fmul_rn(mu[2], uy)), __fmul_rn(mu[3], uz)),
+                              __fmul_rn(0.75f, mu[4])),
+                    __fmul_rn(__fmul_rn(0.5f, p.gbeta), luz));
+                lgb[col] = __dadd_rn(lgb[col], __dmul_rn(0.5 * (double)Th, (double)luz));
                 float og[7];
 #pragma unroll
                 for (int i = 0; i < 7; ++i) og[i] = lTh;
@@ -475,54 +491,60 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     }
     // ---- front of the step before, backwards (lambda_s of level t = Ls)
     if (FRONT) {
-        const double sc = in.sc, sp = in.sp, sq = in.sq;
+        const double sc = in.sc;
+        const float sp = in.sp, sq = in.sq;
         const int k = in.k;
-        double G, dGds, dGdy0 = 0.0, dGdy1 = 0.0, dGdTw = 0.0;
-        // G exactly as the forward computes it (the clamp test below must
-        // agree with the forward's); the derivatives through reciprocals
+        // G and the speed exactly as the forward computes them (the clamp
+        // test below must agree with the forward's); the derivatives through
+        // reciprocals.  Operations rounded one by one here too: the kernels
+        // that run this (with and without the ghost part) then agree.
+        const float G = front_gradient(k, sc, in.y0, in.y1, Tm, Tw);
+        float dGds, dGdy0 = 0.0f, dGdy1 = 0.0f, dGdTw = 0.0f;
         if (k < 0) {
-            G = (Tm - Tw) / sc;
-            const double is = 1.0 / sc;
-            dGds = -(Tm - Tw) * is * is;
+            const float is = __fdiv_rn(1.0f, (float)sc);
+            dGds = __fmul_rn(__fmul_rn(-__fsub_rn(Tm, Tw), is), is);
             dGdTw = -is;
         } else {
-            const double y1 = in.y1, y0 = in.y0, x1 = k + 0.5;
+            const float y1 = in.y1, y0 = in.y0;
+            const double x1 = k + 0.5;
             const double x0 = k >= 1 ? k - 0.5 : 0.0;
-            const double h = x1 - x0, d1 = sc - x1, d0 = sc - x0;
-            G = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
-            const double ih = k >= 1 ? 1.0 : 2.0;  // h is 1 or 1/2
-            const double i0 = 1.0 / d0, i1 = 1.0 / d1;
-            dGdy0 = d1 * ih * i0;
-            dGdy1 = -d0 * ih * i1;
-            dGds = (y0 - Tm) * i0 * i0 + (y1 - Tm) * i1 * i1;
+            const float d1 = (float)(sc - x1), d0 = (float)(sc - x0);
+            const float ih = k >= 1 ? 1.0f : 2.0f;  // h is 1 or 1/2
+            const float i0 = __fdiv_rn(1.0f, d0), i1 = __fdiv_rn(1.0f, d1);
+            dGdy0 = __fmul_rn(__fmul_rn(d1, ih), i0);
+            dGdy1 = -__fmul_rn(__fmul_rn(d0, ih), i1);
+            dGds = __fadd_rn(__fmul_rn(__fmul_rn(__fsub_rn(y0, Tm), i0), i0),
+                             __fmul_rn(__fmul_rn(__fsub_rn(y1, Tm), i1), i1));
         }
-        const double fac = 1.0 + sp * sp + sq * sq;
-        const double v = p.coef * fac * (-G);
-        const double sn = sc + v;
+        const float fac = front_slope_factor(sp, sq);
+        const float v = front_speed(p, fac, G);
+        const double sn = sc + (double)v;
         if (!(sn >= 0.5) || sn > (double)H) {  // clamped: s(t) does not depend on anything
             lams_prev[col] = 0.0;
             wp_prev[col] = 0.0;
             wq_prev[col] = 0.0;
             nd[2] = nd[3] = -1;
         } else {
-            const double a = Ls * p.coef * fac;  // lambda times d v / d(-G)
-            lams_prev[col] = Ls - a * dGds;
-            wp_prev[col] = Ls * p.coef * (-G) * 2.0 * sp;
-            wq_prev[col] = Ls * p.coef * (-G) * 2.0 * sq;
-            lcoef[col] += Ls * fac * (-G);
+            const float af = __fmul_rn(p.coef_f, fac);  // d v / d(-G)
+            const float La = __fmul_rn((float)Ls, af);  // lambda times that
+            const float vG = __fmul_rn(__fmul_rn(p.coef_f, -G), 2.0f);
+            lams_prev[col] = __dsub_rn(Ls, __dmul_rn(Ls, (double)__fmul_rn(af, dGds)));
+            wp_prev[col] = Ls * (double)__fmul_rn(vG, sp);
+            wq_prev[col] = Ls * (double)__fmul_rn(vG, sq);
+            lcoef[col] = __dadd_rn(lcoef[col], __dmul_rn(Ls, (double)__fmul_rn(fac, -G)));
             if (k >= 0) {
-                const float lT1 = (float)(-a * dGdy1);
+                const float lT1 = -__fmul_rn(La, dGdy1);
 #pragma unroll
                 for (int i = 0; i < 7; ++i) add[2][i] = lT1;
                 if (k >= 1) {
-                    const float lT0 = (float)(-a * dGdy0);
+                    const float lT0 = -__fmul_rn(La, dGdy0);
 #pragma unroll
                     for (int i = 0; i < 7; ++i) add[3][i] = lT0;
                 } else {
-                    dthw += -a * dGdy0;
+                    dthw += (double)(-__fmul_rn(La, dGdy0));
                 }
             } else {
-                dthw += -a * dGdTw;
+                dthw += (double)(-__fmul_rn(La, dGdTw));
             }
         }
     }
@@ -621,6 +643,7 @@ __global__ void __launch_bounds__(256) k_sum_into(const double *__restrict__ v, 
 
 struct lbm_tape {
     long long T, C, nseg;
+    long long thw_gen;               // the handle's wall-field generation when recorded
     size_t ck_bytes;
     std::vector<void *> ck;          // device checkpoints, one per segment
     std::vector<int> ck_cur, ck_inflight;
@@ -699,6 +722,7 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
     h->tape = t;
     t->T = steps;
     t->C = ckpt_every;
+    t->thw_gen = h->thw_gen;
     t->nseg = (steps + ckpt_every - 1) / ckpt_every;
     t->ck_bytes = state_layout(h, nullptr, nullptr, nullptr);
     for (long long sgm = 0; sgm < t->nseg; ++sgm) {
@@ -732,6 +756,8 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     if (!h || !seed) return LBM_EINVAL;
     lbm_tape *t = (lbm_tape *)h->tape;
     if (!t) return tape_err(h, LBM_EINVAL, "no recorded run (call lbm_melt_tape_forward first)");
+    if (t->thw_gen != h->thw_gen)
+        return tape_err(h, LBM_EINVAL, "the heated-wall field changed after the recorded run; record it again");
     // the sweep relies on fronts that move at most half a node per step
     {
         const lbm_status s0 = lbm_check_status(h);
@@ -799,36 +825,37 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         if (a.p != (void **)&fin && a.p != (void **)&snap) BCK(cudaMemsetAsync(*a.p, 0, a.b, h->stream), "zero");
     BCK(cudaMemcpyAsync(lams[1], seed, nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         h->stream), "seed");
-    auto snapshot = [&](long long j) -> lbm_status {
-        lbm::Bufs b;
-        std::memset(&b, 0, sizeof b);
-        b.F = h->F; b.G = h->G; b.js = h->js[h->cur];
-        const float *thw = h->thw_cur;
-        float *out = snap + (size_t)j * 26 * N;
-        if (h->precision == 1) {
-            if (h->face == 0) lbm::k_snapshot<__half, 0><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
-            else lbm::k_snapshot<__half, 1><<<grd, blk, 0, h->stream>>>(p, (const __half *)h->F, (const __half *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
-        } else {
-            if (h->face == 0) lbm::k_snapshot<float, 0><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
-            else lbm::k_snapshot<float, 1><<<grd, blk, 0, h->stream>>>(p, (const float *)h->F, (const float *)h->G, b.js, h->nb[h->cur], h->s[h->cur], thw, h->inflight, out, snap_s + (size_t)j * nc, snap_js + (size_t)j * nc, snap_nb + (size_t)j * nc);
-        }
-        TCK(cudaGetLastError(), "snapshot");
-        return LBM_OK;
-    };
+    // One segment: snapshot of its first level, the recomputed steps with a
+    // snapshot after each, then the reverse sweep over its levels.  All of
+    // it goes on stream sm (so that it can be captured into a graph), from
+    // phase (cur, inflight), with the stream-collide grids cut at the run's
+    // height bound; the adjoint buffers alternate as the levels go by.
     const float *thw = h->thw_cur;
-    for (long long sgm = t->nseg - 1; sgm >= 0 && st == LBM_OK; --sgm) {
-        const long long len = std::min(C, t->T - sgm * C);
-        if ((st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
-        h->cur = t->ck_cur[sgm];
-        h->inflight = t->ck_inflight[sgm];
-        h->steps = t->ck_steps[sgm];
-        if ((st = snapshot(0)) != LBM_OK) break;
-        for (long long j = 1; j <= len && st == LBM_OK; ++j) {
-            if ((st = lbm_melt_step(h, 1)) != LBM_OK) break;
-            st = snapshot(j);
+    auto enqueue_segment = [&](long long len, int cur, int inflight, cudaStream_t sm, float *(&lm)[2],
+                               double *(&lms)[2]) -> cudaError_t {
+        auto snapshot = [&](long long j) {
+            float *out = snap + (size_t)j * 26 * N;
+            double *os = snap_s + (size_t)j * nc;
+            int *ojs = snap_js + (size_t)j * nc, *onb = snap_nb + (size_t)j * nc;
+            const int *js = h->js[cur], *nbv = h->nb[cur];
+            const double *sv = h->s[cur];
+            if (h->precision == 1) {
+                const __half *F = (const __half *)h->F, *G = (const __half *)h->G;
+                if (h->face == 0) lbm::k_snapshot<__half, 0><<<grd, blk, 0, sm>>>(p, F, G, js, nbv, sv, thw, inflight, out, os, ojs, onb);
+                else lbm::k_snapshot<__half, 1><<<grd, blk, 0, sm>>>(p, F, G, js, nbv, sv, thw, inflight, out, os, ojs, onb);
+            } else {
+                const float *F = (const float *)h->F, *G = (const float *)h->G;
+                if (h->face == 0) lbm::k_snapshot<float, 0><<<grd, blk, 0, sm>>>(p, F, G, js, nbv, sv, thw, inflight, out, os, ojs, onb);
+                else lbm::k_snapshot<float, 1><<<grd, blk, 0, sm>>>(p, F, G, js, nbv, sv, thw, inflight, out, os, ojs, onb);
+            }
+            return cudaGetLastError();
+        };
+        cudaError_t e = snapshot(0);
+        for (long long j = 1; j <= len && e == cudaSuccess; ++j) {
+            e = lbm_enqueue_step(h, cur, inflight, abound, sm);
+            if (e == cudaSuccess) e = snapshot(j);
         }
-        if (st != LBM_OK) break;
-        for (long long j = len - 1; j >= 0; --j) {
+        for (long long j = len - 1; j >= 0 && e == cudaSuccess; --j) {
             const float *s1 = snap + (size_t)(j + 1) * 26 * N, *s0 = snap + (size_t)j * 26 * N;
             const double *st_s = snap_s + (size_t)j * nc;
             const int *st_js = snap_js + (size_t)j * nc;
@@ -841,26 +868,73 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             const double *st_s_prev = j > 0 ? snap_s + (size_t)(j - 1) * nc : nullptr;
             if (h->face == 0) {
                 if (j == len - 1)
-                    lbm::k_adj_front<0><<<cgrid, cb, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp[pj], wq[pj], lam[1], lthw, lcoef);
-                lbm::k_adj_node<0><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
+                    lbm::k_adj_front<0><<<cgrid, cb, 0, sm>>>(p, s1, st_s, thw, lms[1], lms[0], wp[pj], wq[pj], lm[1], lthw, lcoef);
+                lbm::k_adj_node<0><<<grd, blk, 0, sm>>>(p, s0, st_js, st_nb, lm[1], lm[0], lgpost, lthw, part);
                 if (j > 0)
-                    lbm::k_adj_ghost_front<0><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lam[0], lams[0], lams[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
+                    lbm::k_adj_ghost_front<0><<<cgrid, cb, 0, sm>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lm[0], lms[0], lms[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
                 else
-                    lbm::k_adj_ghost<0><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp[pj], wq[pj]);
+                    lbm::k_adj_ghost<0><<<cgrid, cb, 0, sm>>>(p, s0, st_js, st_s, thw, lgpost, lm[0], lms[0], lthw, lsal, lgb, wp[pj], wq[pj]);
             } else {
                 if (j == len - 1)
-                    lbm::k_adj_front<1><<<cgrid, cb, 0, h->stream>>>(p, s1, st_s, thw, lams[1], lams[0], wp[pj], wq[pj], lam[1], lthw, lcoef);
-                lbm::k_adj_node<1><<<grd, blk, 0, h->stream>>>(p, s0, st_js, st_nb, lam[1], lam[0], lgpost, lthw, part);
+                    lbm::k_adj_front<1><<<cgrid, cb, 0, sm>>>(p, s1, st_s, thw, lms[1], lms[0], wp[pj], wq[pj], lm[1], lthw, lcoef);
+                lbm::k_adj_node<1><<<grd, blk, 0, sm>>>(p, s0, st_js, st_nb, lm[1], lm[0], lgpost, lthw, part);
                 if (j > 0)
-                    lbm::k_adj_ghost_front<1><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lam[0], lams[0], lams[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
+                    lbm::k_adj_ghost_front<1><<<cgrid, cb, 0, sm>>>(p, s0, st_js, st_s, st_s_prev, thw, lgpost, lm[0], lms[0], lms[1], lthw, lsal, lgb, lcoef, wp[pj], wq[pj], wp[pm], wq[pm]);
                 else
-                    lbm::k_adj_ghost<1><<<cgrid, cb, 0, h->stream>>>(p, s0, st_js, st_s, thw, lgpost, lam[0], lams[0], lthw, lsal, lgb, wp[pj], wq[pj]);
+                    lbm::k_adj_ghost<1><<<cgrid, cb, 0, sm>>>(p, s0, st_js, st_s, thw, lgpost, lm[0], lms[0], lthw, lsal, lgb, wp[pj], wq[pj]);
             }
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) { st = tape_err(h, LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e)); break; }
-            std::swap(lam[0], lam[1]);
-            std::swap(lams[0], lams[1]);
+            e = cudaGetLastError();
+            std::swap(lm[0], lm[1]);
+            std::swap(lms[0], lms[1]);
         }
+        return e;
+    };
+    // Full-length segments all run the same launches from the same phase
+    // (and the same parity of the alternating buffers), so each such
+    // combination is captured into a CUDA graph once and replayed: the
+    // host's launches would otherwise bound small cavities.
+    struct SegGraph { int cur, inflight, par; cudaGraphExec_t exec; };
+    std::vector<SegGraph> seg_graphs;
+    float *const lam0_first = lam[0];
+    auto free_graphs = [&]() {
+        for (auto &g : seg_graphs) cudaGraphExecDestroy(g.exec);
+        seg_graphs.clear();
+    };
+    if (!h->cap_stream) BCK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    for (long long sgm = t->nseg - 1; sgm >= 0 && st == LBM_OK; --sgm) {
+        const long long len = std::min(C, t->T - sgm * C);
+        if ((st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
+        const int cur0 = t->ck_cur[sgm], infl0 = t->ck_inflight[sgm];
+        h->steps = t->ck_steps[sgm];
+        cudaError_t e = cudaSuccess;
+        if (len == C && t->nseg > 2) {
+            const int par = lam[0] == lam0_first ? 0 : 1;
+            cudaGraphExec_t exec = nullptr;
+            for (auto &g : seg_graphs)
+                if (g.cur == cur0 && g.inflight == infl0 && g.par == par) exec = g.exec;
+            if (!exec) {
+                float *lm[2] = {lam[0], lam[1]};
+                double *lms[2] = {lams[0], lams[1]};
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    e = enqueue_segment(len, cur0, infl0, h->cap_stream, lm, lms);
+                    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e == cudaSuccess) seg_graphs.push_back({cur0, infl0, par, exec});
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+            if (len & 1) {
+                std::swap(lam[0], lam[1]);
+                std::swap(lams[0], lams[1]);
+            }
+        } else {
+            e = enqueue_segment(len, cur0, infl0, h->stream, lam, lams);
+        }
+        if (e != cudaSuccess) st = tape_err(h, LBM_ECUDA, "adjoint segment: %s", cudaGetErrorString(e));
     }
     if (st == LBM_OK) {
         // parameter sensitivities: acc = {d/ds_nu, d/ds_alpha, d/dcoef, d/dgbeta}
@@ -906,6 +980,7 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     h->inflight = fin_inflight;
     h->steps = fin_steps;
     cudaStreamSynchronize(h->stream);
+    free_graphs();
     cleanup();
     return st != LBM_OK ? st : st2;
 }

@@ -33,6 +33,7 @@ struct lbm_melt {
     float *gpost;
     float *thw_cur, *thw_prev;
     int thw_pending;   // set_hot_wall happened while values were in flight
+    long long thw_gen; // number of set_hot_wall calls (a recorded run keeps the field of its record)
     int thw_last_prev; // set_hot_wall since the last step in the natural layout: thw_prev holds the
                        // field of the last streaming (the Nusselt number's wall value)
     double *nu_dev;    // per-column Nusselt numbers (ncols)
@@ -86,6 +87,10 @@ struct lbm_melt {
 
 // Release a handle's recorded run (defined with the adjoint).
 void lbm_tape_free(lbm_melt *h);
+// Enqueue one step (stream-collide, front, flip) from phase (cur, inflight)
+// on stream st, the stream-collide grid cut at `height`; advances cur and
+// inflight.  No host bookkeeping (step counters, read-backs, report rows).
+cudaError_t lbm_enqueue_step(lbm_melt *h, int &cur, int &inflight, int height, cudaStream_t st);
 // Reads the sticky front status on the handle's stream (synchronises):
 // LBM_EUNSTABLE after a step with |ds| > 1/2, LBM_ENAN after a non-finite
 // front temperature, else LBM_OK.

@@ -334,6 +334,30 @@ __device__ __forceinline__ float node_T(const KP &p, const ST *G, int col, int j
     return sum_T(p, g);
 }
 
+// The Eq. 6 gradient dT/da at the front a = s (R8: the one-sided quadratic
+// through (s, Tm) and the guarded node k with the node below it, or the
+// heated wall (0, Tw) for a missing node; linear through the wall when k <
+// 0), and the front speed ds/dt = coef (1 + s_p^2 + s_q^2)(-dT/da).  FP32
+// with every operation rounded on its own (no contraction into FMAs), so that
+// each kernel that evaluates them (the front update, the ensemble, the
+// adjoint's recomputation) gets the same bits.  With h = x1 - x0,
+// d1 = s - x1, d0 = s - x0: p'(s) = (y0 d1^2 - y1 d0^2 + Tm h (d0 + d1)) /
+// (h d0 d1).
+__device__ __forceinline__ float front_gradient(int k, double sc, float y0, float y1, float Tm, float Tw) {
+    if (k < 0) return __fdiv_rn(__fsub_rn(Tm, Tw), (float)sc);
+    const double x1 = k + 0.5, x0 = k >= 1 ? k - 0.5 : 0.0;
+    const float h = (float)(x1 - x0), d1 = (float)(sc - x1), d0 = (float)(sc - x0);
+    const float num = __fadd_rn(__fsub_rn(__fmul_rn(__fmul_rn(y0, d1), d1), __fmul_rn(__fmul_rn(y1, d0), d0)),
+                                __fmul_rn(__fmul_rn(Tm, h), __fadd_rn(d0, d1)));
+    return __fdiv_rn(num, __fmul_rn(__fmul_rn(h, d0), d1));
+}
+__device__ __forceinline__ float front_slope_factor(float sp, float sq) {
+    return __fadd_rn(__fadd_rn(1.0f, __fmul_rn(sp, sp)), __fmul_rn(sq, sq));
+}
+__device__ __forceinline__ float front_speed(const KP &p, float fac, float G) {
+    return __fmul_rn(__fmul_rn(p.coef_f, fac), -G);
+}
+
 // Highest node at least half a cell below s (centre j + 1/2 <= s - 1/2).
 __device__ __forceinline__ int guarded_node(double s, int H) {
     int k = (int)floor(s - 1.0);
@@ -400,19 +424,8 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     // Then Eq. 6.
     double sn = sc;
     if (move) {
-        float Gr;
-        if (k < 0) {
-            Gr = (Tm - Tw) / (float)sc;
-        } else {
-            // derivative at x2 = s of the quadratic through (x0, y0), (x1, y1),
-            // (x2, Tm): with h = x1 - x0, d1 = x2 - x1, d0 = x2 - x0,
-            // p'(x2) = (y0 d1^2 - y1 d0^2 + Tm h (d0 + d1)) / (h d0 d1)
-            const double x1 = k + 0.5;
-            const double x0 = k >= 1 ? k - 0.5 : 0.0;
-            const float h = (float)(x1 - x0), d1 = (float)(sc - x1), d0 = (float)(sc - x0);
-            Gr = (y0 * d1 * d1 - y1 * d0 * d0 + Tm * h * (d0 + d1)) / (h * d0 * d1);
-        }
-        const float v = p.coef_f * (1.0f + sp * sp + sq * sq) * (-Gr);
+        const float Gr = front_gradient(k, sc, y0, y1, Tm, Tw);
+        const float v = front_speed(p, front_slope_factor(sp, sq), Gr);
         if (!isfinite(Gr)) atomicOr(status, 2);
         else if (!(fabsf(v) <= 0.5f)) atomicOr(status, 1);
         sn = sc + (double)v;

@@ -395,6 +395,10 @@ bool graph_eligible(const lbm_melt *h, long long left) {
 
 lbm_status lbm_check_status(lbm_melt *h) { return check_status(h); }
 
+cudaError_t lbm_enqueue_step(lbm_melt *h, int &cur, int &inflight, int height, cudaStream_t st) {
+    return enqueue_step(h, cur, inflight, height, sc_block(h), st);
+}
+
 
 
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
@@ -817,6 +821,7 @@ LBM_API lbm_status lbm_melt_set_hot_wall(lbm_melt *h, const float *T_h_field, in
         CK(cudaMemcpyAsync(h->thw_prev, h->thw_cur, nc * 4, cudaMemcpyDeviceToDevice, h->stream), "copy wall");
         h->thw_last_prev = 1;
     }
+    h->thw_gen++;
     return copy_in(h, h->thw_cur, T_h_field, nc * 4, ptr_kind);
 }
 
