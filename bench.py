@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the FP16, ensemble and adjoint legs (profiling runs)")
-    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection"],
+    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection", "table1"],
                     help="run one of the extra legs alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=0, help="steps of that leg (0: its default)")
     ap.add_argument("--dump-dir", default=None, help="directory for the convection leg's final front map (.npy)")
@@ -414,6 +414,59 @@ def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
             "workload": "128^3 heated at y=0, Ra 1e5, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1, FP32"}
 
 
+def table1_leg(n=96):
+    """The paper's two convection-melting cases (section 3.2, Table 1): Pr
+    0.02, Ste 0.1, Ra 25000 to Fo 1.00 and Ra 10000 to Fo 1.57 (the same
+    lattice time by Eq. 7), n^3 heated at y = 0, Ma 0.1, front from s0 = 1:
+    the quantities the paper discusses with Figs. 4 and 5 (liquid fraction,
+    heat-surface Nusselt number, front across x, temperature against
+    height) and the run's throughput."""
+    import torch
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    cases = [(1, 0.02, 25000.0, 0.1, 1.00), (2, 0.02, 10000.0, 0.1, 1.57)]
+    out = {}
+    for case, Pr, Ra, Ste, Fo in cases:
+        cav = Cavity(n, n, n, stream=stream.cuda_stream, face=0, Ra=Ra, Pr=Pr, Ste=Ste, Ma=0.1, s0=1.0, derive=True)
+        info = cav.info()
+        steps = int(round(Fo * n * n / info["alpha"] - info["t0"]))
+        cav.set_report(max(1, steps // 10), 16)
+        steps_fo1 = int(round(1.0 * n * n / info["alpha"] - info["t0"]))
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cav.step(steps_fo1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        lf_fo1 = cav.get(T=False, u=False)[3]
+        e0.record(stream)
+        cav.step(steps - steps_fo1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        T, u, S, lf = cav.get()
+        nu, nu_mean = cav.nusselt()
+        rows = cav.get_report()
+        cav.close()
+        zmid = slice(n // 2 - 8, n // 2 + 8)
+        out["case%d" % case] = {
+            "Ra": Ra, "Fo": Fo, "steps": steps, "lattice_time": info["t0"] + steps, "ms": ms,
+            "us_per_step": ms * 1e3 / steps, "liquid_fraction": lf, "liquid_fraction_at_Fo_1": lf_fo1,
+            "nusselt_mean": nu_mean,
+            "nusselt_over_z_vs_x": [[int(x), float(nu[:, x].mean())] for x in range(0, n, 8)],
+            "front_over_z_vs_x": [[int(x), float(S[:, x].mean())] for x in range(0, n, 8)],
+            "front_std_across_x_at_mid_height": float(S[zmid, :].std(axis=1).mean()),
+            "T_near_wall_vs_z": [[int(z), float(T[z, 2, :].mean())] for z in range(0, n, 8)],
+            "liquid_fraction_vs_Fo": [[float(info["alpha"] * (info["t0"] + r[0]) / (n * n)), float(r[1])]
+                                      for r in rows],
+            "nusselt_mean_vs_Fo": [[float(info["alpha"] * (info["t0"] + r[0]) / (n * n)), float(r[7])]
+                                   for r in rows]}
+    out["workload"] = ("%d^3 heated at y=0, Pr 0.02, Ste 0.1, Ma 0.1, front from s0 = 1, FP32; case 1 Ra 25000 "
+                       "to Fo 1.00, case 2 Ra 10000 to Fo 1.57" % n)
+    return out
+
+
 def ensemble_leg(steps=100, n_cav=48, seed=2016):
     """48 seeded cavities of uneven sizes in one persistent launch per run of
     steps, against the same cavities stepped one after another."""
@@ -602,6 +655,7 @@ def run_gpu(args):
         extra["ensemble"] = ensemble_leg()
         extra["adjoint"] = adjoint_leg()
         extra["convection"] = convection_leg(dump_dir=args.dump_dir)
+        extra["table1"] = table1_leg()
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -639,8 +693,8 @@ def run_leg(args):
     import torch
     torch.cuda.set_device(0)
     legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg,
-            "convection": convection_leg}
-    kw = {"steps": args.leg_steps} if args.leg_steps > 0 else {}
+            "convection": convection_leg, "table1": table1_leg}
+    kw = {"steps": args.leg_steps} if args.leg_steps > 0 and args.leg != "table1" else {}
     if args.leg == "convection":
         kw["dump_dir"] = args.dump_dir
     print(json.dumps({"leg": args.leg, **legs[args.leg](**kw)}))

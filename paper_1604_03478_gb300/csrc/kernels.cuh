@@ -162,9 +162,23 @@ __device__ __forceinline__ float wall_value(const KP &p, int dir, float v, float
     return w == 3 ? v : -v + 2.0f * w7(dir) * ((w == 1 ? Th_col : p.Tc) - p.Tm);
 }
 
+// Across an x wall (x = 0 for e_x = +1 upstream, x = nx - 1 for e_x = -1):
+// the only walls a warp's nodes (32 consecutive x at one height and plane)
+// do not all share.
+__device__ __forceinline__ bool xwall(int ex_up, bool xlo, bool xhi) {
+    return ex_up > 0 ? xlo : (ex_up < 0 ? xhi : false);
+}
+
 // TAB: take the interior link offsets from the precomputed tables of KP
 // (kernel parameters: constant-bank operands); false computes them from the
 // extents, which keeps them out of registers when KP lives in shared memory.
+//
+// Fast path: a liquid node off the walls of the heating axis and of the
+// other in-plane axis and at least one node below the lowest first-solid
+// node of its 3x3 neighbour columns, so that every link streams except those
+// across an x wall, which bounce back (no-slip for f, adiabatic for g).  The
+// x walls are taken by selects inside the fast path, so that the warps that
+// hold x = 0 or x = nx - 1 do not split between two paths.
 template <typename ST, int FACE, bool TAB = true>
 __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
                                          const int *__restrict__ nb, const float *__restrict__ gpost,
@@ -176,21 +190,34 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
     const int jsc = __ldg(js + col);
     const int nbv = __ldg(nb + col);
     const int q = FACE == 0 ? z : y, nq = FACE == 0 ? p.nz : p.ny;
-    const bool off_walls = x >= 1 && x <= p.nx - 2 && q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
+    const bool off_qa = q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
+    const bool off_walls = off_qa && x >= 1 && x <= p.nx - 2;
+    const bool xlo = x == 0, xhi = x == p.nx - 1;
     ST *const Fc = F + c;
     ST *const Gc = G + c;
     float g[7];
     if (a < jsc) {
-        // interior: off the walls and at least one node below the lowest
-        // first-solid node of the 3x3 neighbour columns: every link streams
-        const bool interior = off_walls && a + 1 < (nbv >> 16);
+        const bool fast = off_qa && a + 1 < (nbv >> 16);
         float f[19];
         unsigned lm = 0x7fffeu, im = 0x7eu;
-        if (interior) {
+        if (fast) {
 #pragma unroll
             for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(Fc + fin_off<FACE, TAB>(p, lk, i));
 #pragma unroll
             for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(Gc + gin_off<FACE, TAB>(p, lk, i));
+            // Across an x wall the pull above read the neighbouring row's
+            // node instead (an in-bounds element of the same direction array:
+            // the node is off the walls of the other two axes); bounce-back
+            // replaces it with the value parked in the node's own slot i
+            // (no-slip for f, adiabatic for g).
+            if (xlo | xhi) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i)
+                    if (xwall(ex(i), xlo, xhi)) f[i] = Store<ST>::ld(Fc + i * p.ld);
+#pragma unroll
+                for (int i = 1; i < 7; ++i)
+                    if (xwall(tx(i), xlo, xhi)) g[i] = Store<ST>::ld(Gc + i * p.ld);
+            }
         } else {
             lm = link_mask<FACE>(p, js, x, y, z);
             im = inside_mask(p, x, y, z);
@@ -208,11 +235,17 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
             }
         }
         collide(p, f, g);
-        if (interior) {
+        if (fast) {
+            Store<ST>::st_stream(Fc, f[0]);
 #pragma unroll
-            for (int i = 0; i < 19; ++i) Store<ST>::st_stream(Fc + fout_off<FACE, TAB>(p, lk, i), f[i]);
+            for (int i = 1; i < 19; ++i)  // towards an x wall: stays in slot opp(i)
+                Store<ST>::st_stream(xwall(-ex(i), xlo, xhi) ? Fc + opp(i) * p.ld : Fc + fout_off<FACE, TAB>(p, lk, i),
+                                     f[i]);
+            Store<ST>::st_stream(Gc, g[0]);
 #pragma unroll
-            for (int i = 0; i < 7; ++i) Store<ST>::st_stream(Gc + gout_off<FACE, TAB>(p, lk, i), g[i]);
+            for (int i = 1; i < 7; ++i)
+                Store<ST>::st_stream(xwall(-tx(i), xlo, xhi) ? Gc + opp7(i) * p.ld : Gc + gout_off<FACE, TAB>(p, lk, i),
+                                     g[i]);
             return;
         }
         Store<ST>::st_stream(Fc, f[0]);
