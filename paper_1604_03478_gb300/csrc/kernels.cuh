@@ -51,6 +51,15 @@ template <int FACE, bool TAB> __device__ __forceinline__ long long gout_off(cons
     return TAB ? lk->gout[i] : i * p.ld + off7<FACE>(p, i);
 }
 
+// Element base[c + off] with the index arithmetic done in IX: unsigned (32
+// bits, for states whose every element index fits) or long long.  With
+// 32-bit indices a link offset enters the address as one 32-bit add of a
+// kernel-parameter operand.
+template <typename IX, typename ST>
+__device__ __forceinline__ ST *elem(ST *base, IX c, long long off) {
+    return base + (IX)(c + (IX)off);
+}
+
 // Post-collision shifted g of a solid node: the ghost node (first solid node
 // of its column) takes the populations prepared by k_front; deeper nodes are
 // at rest at Tm, i.e. zero.
@@ -70,10 +79,10 @@ __device__ __forceinline__ bool deep_solid(const KP &p, int a, int nbv) {
 }
 
 // ------------------------------------------------------------- even step
-template <typename ST, int FACE>
+template <typename ST, int FACE, typename IX = long long>
 __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
                                           const int *__restrict__ nb, const float *__restrict__ gpost, int x, int y, int z) {
-    const long long c = node_index(p, x, y, z);
+    const IX c = (IX)node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
     const int jsc = __ldg(js + col);
@@ -81,18 +90,18 @@ __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *_
     if (a < jsc) {
         float f[19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(F + i * p.ld + c);
+        for (int i = 0; i < 19; ++i) f[i] = Store<ST>::ld(elem<IX>(F, c, i * p.ld));
 #pragma unroll
-        for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(G + i * p.ld + c);
+        for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(elem<IX>(G, c, i * p.ld));
         collide(p, f, g);
 #pragma unroll
-        for (int i = 0; i < 19; ++i) Store<ST>::st_stream(F + opp(i) * p.ld + c, f[i]);
+        for (int i = 0; i < 19; ++i) Store<ST>::st_stream(elem<IX>(F, c, opp(i) * p.ld), f[i]);
     } else {
         if (deep_solid(p, a, __ldg(nb + col))) return;
         solid_post(p, a == jsc, gpost, col, g);
     }
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<ST>::st_stream(G + opp7(i) * p.ld + c, g[i]);
+    for (int i = 0; i < 7; ++i) Store<ST>::st_stream(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
 }
 
 // Stream-collide grid: blocks of blockDim.x x blockDim.y nodes of one plane
@@ -123,12 +132,12 @@ __device__ __forceinline__ bool k1_node(const KP &p, const int *jmax, int &x, in
 // blocks, no spills; forced to 8 it loses 1%).
 template <typename ST> constexpr int k1_min_blocks() { return sizeof(ST) == 2 ? 8 : 0; }
 
-template <typename ST, int FACE>
+template <typename ST, int FACE, typename IX>
 __global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const int *__restrict__ nb,
                                               const float *__restrict__ gpost, const int *jmax) {
     int x, y, z;
-    if (k1_node<FACE>(p, jmax, x, y, z)) even_node<ST, FACE>(p, F, G, js, nb, gpost, x, y, z);
+    if (k1_node<FACE>(p, jmax, x, y, z)) even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
 }
 
 

@@ -7,18 +7,28 @@
 
 namespace lbm {
 
-template <typename ST>
-cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
-    const dim3 grd = k1_grid(p, blk, face, b.k1_height);
+template <typename ST, typename IXE>
+static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, dim3 blk, cudaStream_t st) {
     const int *jm = p.skip_deep ? b.jmax : nullptr;
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
         if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        else k_even<ST, 0, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
         if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        else k_even<ST, 1, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
     }
+}
+
+// The even step indexes in 32 bits whenever every index of the 19 direction
+// arrays of F fits (19 ld < 2^32: cavities up to about 2.2e8 nodes), else in
+// 64 bits (FP16 storage 2% faster at 256^3; the odd step ran slower with
+// 32-bit indices, 0.258 against 0.245 ms in FP32, and keeps 64-bit ones).
+template <typename ST>
+cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
+    const dim3 grd = k1_grid(p, blk, face, b.k1_height);
+    if (19LL * p.ld < (1LL << 32)) launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
+    else launch_sc<ST, long long>(p, face, odd, b, grd, blk, st);
     return cudaGetLastError();
 }
 

@@ -295,6 +295,76 @@ __device__ __forceinline__ void add_back7(float (&g)[7], const float (&c)[7]) {
     }
 }
 
+// ------------------------------------- transforms with shared sub-sums
+// m = M f and f += M^T c written out by hand over the pair sums S and
+// differences D, sharing the partial sums that several rows (or, for the
+// back-transform, several pairs) have in common: about 140 additions and
+// multiplications for both instead of about 240 when every row and every
+// pair is summed on its own.  Pair order: x, y, z axes, then the diagonals
+// with first members 7 (1,1,0), 8 (-1,1,0), 11 (1,0,1), 12 (-1,0,1),
+// 15 (0,1,1), 16 (0,-1,1).  The coefficients are the d'Humieres rows of
+// mpoly at those first members.
+__host__ __device__ __forceinline__ void moments_shared(float f0, const float (&S)[9], const float (&D)[9],
+                                                        float (&m)[19]) {
+    const float Sx = S[0], Sy = S[1], Sz = S[2], S7 = S[3], S8 = S[4], S11 = S[5], S12 = S[6], S15 = S[7], S16 = S[8];
+    const float Dx = D[0], Dy = D[1], Dz = D[2], D7 = D[3], D8 = D[4], D11 = D[5], D12 = D[6], D15 = D[7], D16 = D[8];
+    const float Sxy = S7 + S8, Sxz = S11 + S12, Syz = S15 + S16;
+    const float Sax = Sx + Sy + Sz, Sdg = Sxy + Sxz + Syz;
+    m[0] = f0 + Sax + Sdg;
+    m[1] = fmaf(8.0f, Sdg, fmaf(-11.0f, Sax, -30.0f * f0));
+    m[2] = fmaf(-4.0f, Sax, fmaf(12.0f, f0, Sdg));
+    const float a9 = fmaf(2.0f, Sx, -Sy) - Sz, d9 = fmaf(-2.0f, Syz, Sxy + Sxz);
+    m[9] = a9 + d9;
+    m[10] = fmaf(-2.0f, a9, d9);
+    const float a11 = Sy - Sz, d11 = Sxy - Sxz;
+    m[11] = a11 + d11;
+    m[12] = fmaf(-2.0f, a11, d11);
+    m[13] = S7 - S8;
+    m[14] = S15 - S16;
+    m[15] = S11 - S12;
+    const float A = D7 - D8, B = D11 - D12, Xd = A + B;
+    m[3] = Dx + Xd;
+    m[4] = fmaf(-4.0f, Dx, Xd);
+    m[16] = A - B;
+    const float C = D7 + D8, E = D15 - D16, Yd = C + E;
+    m[5] = Dy + Yd;
+    m[6] = fmaf(-4.0f, Dy, Yd);
+    m[17] = E - C;
+    const float G = D11 + D12, H = D15 + D16, Zd = G + H;
+    m[7] = Dz + Zd;
+    m[8] = fmaf(-4.0f, Dz, Zd);
+    m[18] = G - H;
+}
+
+// f += M^T c for c with c[0] = c[3] = c[5] = 0 (mass and in-plane momentum
+// are not changed; c[7], the z momentum, carries the force).
+__host__ __device__ __forceinline__ void add_back_shared(float (&f)[19], const float (&c)[19]) {
+    f[0] = fmaf(12.0f, c[2], fmaf(-30.0f, c[1], f[0]));
+    // even rows
+    const float Kax = fmaf(-4.0f, c[2], -11.0f * c[1]), Kdg = fmaf(8.0f, c[1], c[2]);
+    const float b1 = fmaf(-2.0f, c[10], c[9]), b2 = c[9] + c[10];
+    const float b3 = fmaf(-2.0f, c[12], c[11]), b4 = c[11] + c[12];
+    const float Ex = fmaf(2.0f, b1, Kax), Ky = Kax - b1, Ey = Ky + b3, Ez = Ky - b3;
+    const float K1 = Kdg + b2, K2 = K1 + b4, K3 = K1 - b4, K4 = fmaf(-2.0f, b2, Kdg);
+    const float E7 = K2 + c[13], E8 = K2 - c[13], E11 = K3 + c[15], E12 = K3 - c[15];
+    const float E15 = K4 + c[14], E16 = K4 - c[14];
+    // odd rows
+    const float Ox = -4.0f * c[4], Oy = -4.0f * c[6], Oz = fmaf(-4.0f, c[8], c[7]);
+    const float P = c[4] + c[16], Q = c[6] - c[17], Pp = c[4] - c[16], Qp = c[6] + c[17];
+    const float c78 = c[7] + c[8], R = c78 + c[18], Rp = c78 - c[18];
+    const float O7 = P + Q, O8 = Q - P, O11 = Pp + R, O12 = R - Pp, O15 = Qp + Rp, O16 = Rp - Qp;
+    // pairs (first member, opposite): (1,2) (3,4) (5,6) (7,10) (8,9) (11,14) (12,13) (15,18) (16,17)
+    f[1] += Ex + Ox;   f[2] += Ex - Ox;
+    f[3] += Ey + Oy;   f[4] += Ey - Oy;
+    f[5] += Ez + Oz;   f[6] += Ez - Oz;
+    f[7] += E7 + O7;   f[10] += E7 - O7;
+    f[8] += E8 + O8;   f[9] += E8 - O8;
+    f[11] += E11 + O11; f[14] += E11 - O11;
+    f[12] += E12 + O12; f[13] += E12 - O12;
+    f[15] += E15 + O15; f[18] += E15 - O15;
+    f[16] += E16 + O16; f[17] += E16 - O16;
+}
+
 // -------------------------------------------------------------- collision
 // One liquid node: shifted populations in, shifted post-collision out.
 //   T = Tm + sum gh;  F = g beta (T - Tm) z-hat (Boussinesq, gravity -z);
@@ -315,7 +385,7 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
         S[P] = f[pf(P)] + f[opp(pf(P))];
         D[P] = f[pf(P)] - f[opp(pf(P))];
     }
-    moments_pairs<0>(f[0], S, D, m);
+    moments_shared(f[0], S, D, m);
     const float rho_h = m[0];
     const float ux = m[3], uy = m[5], uz = m[7] + 0.5f * Fz;
     const float uu = ux * ux + uy * uy + uz * uz;
@@ -342,8 +412,7 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
     d[18] = -p.s_m * m[18];
     float c[19];
     scale_by_inverse_norms<0>(d, c);
-    f[0] = pcol<0, 0, false>(c, f[0]);
-    add_back_pairs<0>(f, c);
+    add_back_shared(f, c);
 
     float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
     float n4 = 6.0f * g[0] - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6]);
