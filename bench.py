@@ -535,12 +535,28 @@ def adjoint_leg(steps=4000, n=96):
             res["backward"] = (time.perf_counter() - t0) * 1e3
             res["dL_dRa"] = par["Ra"]
             res["grad_norm_wall"] = float(np.linalg.norm(dth))
+            res["dL_dv1"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 7))
+            res["dL_dv2"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 8))
         cav.close()
-    return {"cube": n, "steps": steps, "forward_ms": res["plain"], "recorded_forward_ms": res["tape"],
-            "backward_ms": res["backward"], "adjoint_forward_ratio": res["backward"] / res["plain"],
-            "total_over_forward": (res["tape"] + res["backward"]) / res["plain"],
-            "dL_dRa": res["dL_dRa"], "grad_norm_wall": res["grad_norm_wall"],
-            "loss": "final liquid fraction", "checkpoints": "every ceil(sqrt(steps)) steps"}
+    out = {"cube": n, "steps": steps, "forward_ms": res["plain"], "recorded_forward_ms": res["tape"],
+           "backward_ms": res["backward"], "adjoint_forward_ratio": res["backward"] / res["plain"],
+           "total_over_forward": (res["tape"] + res["backward"]) / res["plain"],
+           "dL_dRa": res["dL_dRa"], "grad_norm_wall": res["grad_norm_wall"],
+           "dL_dv1": res["dL_dv1"], "dL_dv2": res["dL_dv2"],
+           "loss": "final liquid fraction", "checkpoints": "every ceil(sqrt(steps)) steps",
+           "directions": "v1, v2 = N(0, 1) per wall column, seeds 7 and 8"}
+    if steps == 4000 and n == 96:
+        # the FP64 oracle's complex-step values for this workload
+        golden = {}
+        with open(os.path.join(ROOT, "tests", "golden", "adjoint_96cube_4000steps.txt")) as f:
+            for ln in f:
+                if ln.strip() and not ln.startswith("#"):
+                    k, v = ln.split()
+                    golden[k] = float(v)
+        out["vs_oracle_tangent"] = {k: abs(out[a] / golden[b] - 1.0) for k, a, b in
+                                    (("rel_err_dRa", "dL_dRa", "dlf_dRa"), ("rel_err_dv1", "dL_dv1", "dlf_dv1"),
+                                     ("rel_err_dv2", "dL_dv2", "dlf_dv2"))}
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm

@@ -20,8 +20,9 @@ front from s0 = 1, 4000 steps, heated wall at 1 + N(0, 0.01^2) per column
   whose wall is 1 + N(0, 0.01^2) with seed 11 (a reachable target), and its
   derivatives along dRa and the seed-7 direction, 2 (S - S*) . dS.
 
-Command (about an hour on 8 host cores):
-    python oracle/make_golden_adjoint.py
+Command (about an hour on 8 host cores; with --cache DIR each run's result
+is kept in DIR and a rerun resumes from there):
+    python oracle/make_golden_adjoint.py [--cache DIR]
 """
 from __future__ import annotations
 
@@ -61,7 +62,22 @@ def _real_run(wall):
     return S.ravel(), lf
 
 
+def _cached(cache, name, fn):
+    """fn() -> tuple of arrays/floats, stored under cache/name.npz."""
+    if cache:
+        path = os.path.join(cache, name + ".npz")
+        if os.path.exists(path):
+            d = np.load(path)
+            return tuple(d["v%d" % i] for i in range(len(d.files)))
+    out = tuple(np.asarray(v) for v in fn())
+    if cache:
+        os.makedirs(cache, exist_ok=True)
+        np.savez(os.path.join(cache, name + ".npz"), **{"v%d" % i: v for i, v in enumerate(out)})
+    return out
+
+
 def main():
+    cache = sys.argv[sys.argv.index("--cache") + 1] if "--cache" in sys.argv else None
     inp = _inputs()
     oracle.build()
     ncols = N * N
@@ -74,19 +90,23 @@ def main():
     def log(msg):
         print("[%6.0f s] %s" % (time.time() - t0, msg), flush=True)
 
-    S, dS_ra, lf, dlf_ra = oracle.tangent(N, N, N, STEPS, dRa=1.0, wall=wall, **CASE)
+    S, dS_ra, lf, dlf_ra = _cached(cache, "tl_ra", lambda: oracle.tangent(N, N, N, STEPS, dRa=1.0, wall=wall, **CASE))
+    S, dS_ra, lf, dlf_ra = S.ravel(), dS_ra.ravel(), float(lf), float(dlf_ra)
     log("tangent along Ra: lf %.12g, dlf %.12g" % (lf, dlf_ra))
-    _, dS_v1, _, dlf_v1 = oracle.tangent(N, N, N, STEPS, dThw=v1, wall=wall, **CASE)
+    _, dS_v1, _, dlf_v1 = _cached(cache, "tl_v1", lambda: oracle.tangent(N, N, N, STEPS, dThw=v1, wall=wall, **CASE))
+    dS_v1, dlf_v1 = dS_v1.ravel(), float(dlf_v1)
     log("tangent along v1: dlf %.12g" % dlf_v1)
-    _, _, _, dlf_v2 = oracle.tangent(N, N, N, STEPS, dThw=v2, wall=wall, **CASE)
+    _, _, _, dlf_v2 = _cached(cache, "tl_v2", lambda: oracle.tangent(N, N, N, STEPS, dThw=v2, wall=wall, **CASE))
+    dlf_v2 = float(dlf_v2)
     log("tangent along v2: dlf %.12g" % dlf_v2)
-    Sp, lfp = _real_run(wall + EPS * v1)
-    Sm, lfm = _real_run(wall - EPS * v1)
+    Sp, lfp = _cached(cache, "fd_plus", lambda: _real_run(wall + EPS * v1))
+    Sm, lfm = _cached(cache, "fd_minus", lambda: _real_run(wall - EPS * v1))
+    lfp, lfm = float(lfp), float(lfm)
     fd = (lfp - lfm) / (2.0 * EPS)
     js = lambda s: np.clip(np.ceil(s - 0.5), 0, N).astype(np.int64)  # noqa: E731
     flips = int(np.count_nonzero(js(Sp) != js(Sm))) + int(np.count_nonzero(js(Sp) != js(S)))
     log("central differences along v1: %.12g (columns with another final count: %d)" % (fd, flips))
-    St, _ = _real_run(target_wall)
+    St, _ = _cached(cache, "target", lambda: _real_run(target_wall))
     r = S - St
     L2 = float(r @ r)
     dL2_ra = float(2.0 * r @ dS_ra)

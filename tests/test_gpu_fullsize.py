@@ -105,3 +105,53 @@ def test_adjoint_96cube_against_tangent_oracle(lib, orc):
     v = inputs.gaussian_field(n * n, 1.0, 7)
     _, _, _, dlf_v = orc.tangent(n, n, n, steps, dThw=v, **kw)
     assert float(dth.ravel() @ v) == pytest.approx(dlf_v, rel=1e-3)
+
+
+def _golden_adjoint():
+    import os
+    from conftest import GOLDEN
+    g = {}
+    with open(os.path.join(GOLDEN, "adjoint_96cube_4000steps.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                g[k] = float(v)
+    return g
+
+
+def test_adjoint_96cube_4000_steps_against_golden(lib):
+    """The adjoint workload as the benchmark runs it: 96^3, Ra 1e5, Pr 0.02,
+    Ste 0.1, front from s0 = 1, 4000 steps with sqrt(N) checkpoints, heated
+    wall 1 + N(0, 0.01^2) per column (seed 5).  The gradient of the final
+    liquid fraction along Ra and along two seeded wall directions, and of
+    the L2 mismatch to the final front of a run with wall seed 11, against
+    the FP64 oracle's complex-step tangent-linear values (stored by
+    oracle/make_golden_adjoint.py; central differences agree with them to
+    1e-4), 1e-3 relative."""
+    from paper_1604_03478_gb300 import inputs
+    g = _golden_adjoint()
+    n, steps = 96, 4000
+    kw = dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
+    wall = (1.0 + inputs.gaussian_field(n * n, 0.01, 5)).astype(np.float32)
+    target = lib(n, n, n, **kw)
+    target.set_hot_wall((1.0 + inputs.gaussian_field(n * n, 0.01, 11)).astype(np.float32))
+    target.step(steps)
+    S_target = target.get(T=False, u=False)[2].ravel()
+    target.close()
+    cav = lib(n, n, n, **kw)
+    cav.set_hot_wall(wall)
+    cav.tape_forward(steps)
+    _, _, S, lf = cav.get(T=False, u=False)
+    assert lf == pytest.approx(g["liquid_fraction"], rel=1e-4)
+    dth, par = cav.tape_backward(np.full(cav.ncols, 1.0 / (cav.H * cav.ncols)))
+    v1 = inputs.gaussian_field(n * n, 1.0, 7)
+    v2 = inputs.gaussian_field(n * n, 1.0, 8)
+    assert par["Ra"] == pytest.approx(g["dlf_dRa"], rel=1e-3)
+    assert float(dth.ravel() @ v1) == pytest.approx(g["dlf_dv1"], rel=1e-3)
+    assert float(dth.ravel() @ v2) == pytest.approx(g["dlf_dv2"], rel=1e-3)
+    r = S.ravel() - S_target
+    assert float(r @ r) == pytest.approx(g["mismatch_L2"], rel=1e-3)
+    dth2, par2 = cav.tape_backward(2.0 * r)
+    assert float(dth2.ravel() @ v1) == pytest.approx(g["dL2_dv1"], rel=1e-3)
+    assert par2["Ra"] == pytest.approx(g["dL2_dRa"], rel=1e-3)
+    cav.close()

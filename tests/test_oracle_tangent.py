@@ -75,3 +75,24 @@ def test_tangent_conduction_closed_form(orc):
     dlam = (1 / np.sqrt(np.pi)) / F1
     ds_exact = 2 * np.sqrt(a * t) * dlam * Ste / 1.0
     assert float(dS.ravel()[0]) == pytest.approx(ds_exact, rel=0.05)
+
+
+def test_golden_adjoint_values_are_consistent():
+    """The stored gradients of the 96^3 x 4000-step adjoint workload
+    (tests/golden/adjoint_96cube_4000steps.txt, written from the oracle by
+    oracle/make_golden_adjoint.py): the complex-step derivative along the
+    seed-7 wall direction agrees with the central differences of the real
+    oracle (no column ended with another liquid count), to the accuracy a
+    difference quotient with eps = 1e-9 allows."""
+    from conftest import GOLDEN
+    import os
+    g = {}
+    with open(os.path.join(GOLDEN, "adjoint_96cube_4000steps.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                g[k] = float(v)
+    assert g["fd_count_changes"] == 0
+    assert g["fd_dlf_dv1"] == pytest.approx(g["dlf_dv1"], rel=2e-4)
+    assert 0.05 < g["liquid_fraction"] < 0.2
+    assert g["dlf_dRa"] < 0 and g["dL2_dv1"] < 0
