@@ -270,7 +270,7 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def precision_leg(steps=200, twin_steps=400):
+def precision_leg(steps=200, twin_steps=(400, 1000, 2000)):
     """The precision study: FP32 and FP16 storage at 256^3 with the heated
     wall at the side (y = 0, the benchmark workload) and at the bottom
     (z = 0, Rayleigh-Benard-like), throughput and roofline of each, and the
@@ -304,21 +304,38 @@ def precision_leg(steps=200, twin_steps=400):
                                                     "bytes_per_liquid_node": per_liq}
 
     def twin(face):
+        """Errors of both storages against the oracle on a 64^3 twin at
+        several horizons, the largest split by region: the liquid nodes next
+        to the heated wall (3 layers), those within 3 nodes below the front,
+        and the bulk between."""
         n = 64
         case = dict(CASE, face=face, s0=0.4 * n)
         o = oracle.Oracle(n, n, n, **case)
-        o.step(twin_steps)
-        To, uo, So, lfo = o.get()
+        gpu = {prec: Cavity(n, n, n, precision=prec, stream=stream.cuda_stream, **case) for prec in (0, 1)}
+        err = {"fp32_twin_error": {}, "fp16_twin_error": {}}
+        done = 0
+        for horizon in twin_steps:
+            o.step(horizon - done)
+            for c in gpu.values():
+                c.step(horizon - done)
+            done = horizon
+            To, uo, So, lfo = o.get()
+            H = n
+            a = (np.arange(n)[None, :, None] if face == 0 else np.arange(n)[:, None, None]) * np.ones(To.shape)
+            s_node = (So[:, None, :] if face == 0 else So[None, :, :]) * np.ones(To.shape)
+            liq = a + 0.5 < s_node
+            regions = {"wall_layer": liq & (a < 3), "front_layer": liq & (a + 0.5 >= s_node - 3.0),
+                       "bulk": liq & (a >= 3) & (a + 0.5 < s_node - 3.0)}
+            for prec, name in ((0, "fp32"), (1, "fp16")):
+                Tg, ug, Sg, lfg = gpu[prec].get()
+                dT = np.abs(Tg - To)
+                e = {"max_abs_dT": float(dT.max()), "max_abs_du": float(np.abs(ug - uo).max()),
+                     "abs_d_liquid_fraction": abs(lfg - lfo)}
+                e["max_abs_dT_by_region"] = {k: float(dT[m].max()) if m.any() else 0.0 for k, m in regions.items()}
+                err["%s_twin_error" % name]["%d_steps" % horizon] = e
         o.close()
-        err = {}
-        for prec, name in ((0, "fp32"), (1, "fp16")):
-            c = Cavity(n, n, n, precision=prec, stream=stream.cuda_stream, **case)
-            c.step(twin_steps)
-            Tg, ug, Sg, lfg = c.get()
+        for c in gpu.values():
             c.close()
-            err["%s_twin_error" % name] = {"max_abs_dT": float(np.abs(Tg - To).max()),
-                                           "max_abs_du": float(np.abs(ug - uo).max()),
-                                           "abs_d_liquid_fraction": abs(lfg - lfo)}
         return err
 
     out = {}
@@ -329,7 +346,9 @@ def precision_leg(steps=200, twin_steps=400):
     bottom["fp16_mlups"], bottom["fp16_roofline"] = throughput(1, 1)
     bottom.update(twin(1))
     out["bottom_heated"] = bottom
-    out["twin"] = "64^3, %d steps from the same initial state, against the FP64 oracle" % twin_steps
+    out["twin"] = ("64^3 twin of each workload (same parameters, front at 0.4 H), %s steps from the same initial "
+                   "state, against the FP64 oracle; FP16 stores g shifted by the mid temperature (Th + Tm) / 2"
+                   % ", ".join(str(t) for t in twin_steps))
     return out
 
 
@@ -467,12 +486,18 @@ def table1_leg(n=96):
     return out
 
 
-def ensemble_leg(steps=100, n_cav=48, seed=2016):
-    """48 seeded cavities of uneven sizes in one persistent launch per run of
-    steps, against the same cavities stepped one after another."""
+def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
+    """48 seeded cavities of uneven sizes advanced by the persistent kernel
+    for the configured 10000 steps (replayed from its captured graph), then
+    the same cavities stepped one after another (each by its own step-by-step
+    or graph-replayed launches) over seq_steps.  MLUPS count liquid
+    node-updates (liquid counts averaged over each run); the roofline
+    fraction is the ensemble's whole step (all three phases) against the
+    stream-collide's 208 B per liquid node (28 B per active solid node)."""
     import torch
     from paper_1604_03478_gb300 import Ensemble, autotune, inputs
     stream = torch.cuda.current_stream()
+    peak, _ = hbm_peak()
     draws = inputs.ensemble(n_cav, seed)
     cases = [dict(nx=d["n"], ny=d["n"], nz=d["n"], face=d["face"], Ra=d["Ra"], Pr=0.02, Ste=d["Ste"], Ma=0.1,
                   s0=0.4 * d["n"], derive=True) for d in draws]
@@ -481,7 +506,17 @@ def ensemble_leg(steps=100, n_cav=48, seed=2016):
     ens.step(4)
     ens.sync()
     members = [ens.member(k) for k in range(n_cav)]
-    n_liq = sum(m.totals()["n_liquid"] for m in members)
+
+    def counts():
+        liq = sol = 0
+        for m in members:
+            S = m.get(T=False, u=False)[2]
+            a, b = liquid_counts(S, m.H)
+            liq += a
+            sol += b
+        return liq, sol
+
+    c0 = counts()
     e0, e1 = _events()
     e0.record(stream)
     ens.step(steps)
@@ -489,17 +524,28 @@ def ensemble_leg(steps=100, n_cav=48, seed=2016):
     ens.sync()
     torch.cuda.synchronize()
     ms_ens = e0.elapsed_time(e1)
+    c1 = counts()
+    liq_ens = 0.5 * (c0[0] + c1[0])
+    sol_ens = 0.5 * (c0[1] + c1[1])
     e0.record(stream)
     for m in members:
-        m.step(steps)
+        m.step(seq_steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
+    c2 = counts()
+    liq_seq = 0.5 * (c1[0] + c2[0])
     info = ens.info()
     ens.close()
-    return {"cavities": n_cav, "nodes": info["nodes"], "liquid_nodes": n_liq, "steps": steps,
-            "mlups": n_liq * steps / (ms_ens * 1e-3) / 1e6, "sequential_mlups": n_liq * steps / (ms_seq * 1e-3) / 1e6,
-            "speedup_vs_sequential": ms_seq / ms_ens, "launch": {"block": shape[0], "nodes_per_thread": shape[1]},
+    mlups = liq_ens * steps / (ms_ens * 1e-3) / 1e6
+    seq_mlups = liq_seq * seq_steps / (ms_seq * 1e-3) / 1e6
+    gbs = (208.0 * liq_ens + 28.0 * sol_ens) * steps / (ms_ens * 1e-3) / 1e9
+    return {"cavities": n_cav, "nodes": info["nodes"], "liquid_nodes": liq_ens, "steps": steps,
+            "mlups": mlups, "sequential_mlups": seq_mlups, "sequential_steps": seq_steps,
+            "speedup_vs_sequential": mlups / seq_mlups,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "timed": "whole ensemble step (stream-collide, front and flip phases with their barriers)"},
+            "launch": {"block": shape[0], "nodes_per_thread": shape[1]},
             "workload": "sizes uniform in {48,64,96,128,160}, Ra log-uniform [1e4,1e6], Ste U[0.05,0.2], "
                         "Pr 0.02, heated face y0 or z0, seed %d, front at 0.4 H, FP32" % seed}
 

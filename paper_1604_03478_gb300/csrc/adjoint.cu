@@ -85,8 +85,8 @@ __device__ __forceinline__ void collide_adjoint(const KP &p, const float (&f)[19
                                                 float (&og)[7], float &dsnu, float &dsal, float &dgb) {
     // forward quantities
     const float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-    const float T = Th + p.Tm;
-    const float Fz = p.gbeta * Th;
+    const float T = Th + p.Ts;
+    const float Fz = p.gbeta * (Th - p.dTms);
     float S[9], D[9], m[19];
 #pragma unroll
     for (int P = 0; P < 9; ++P) {
@@ -164,7 +164,7 @@ __device__ __forceinline__ void collide_adjoint(const KP &p, const float (&f)[19
     // through u_z = j_z + F/2 and F = g beta (T - Tm)
     lFz += 0.5f * luz;
     lTh += p.gbeta * lFz;
-    dgb += Th * lFz;
+    dgb += (Th - p.dTms) * lFz;
     lm[0] = lrho;
     lm[3] = lux;
     lm[5] = luy;
@@ -189,7 +189,7 @@ __device__ __forceinline__ float snap_T(const KP &p, const float *snap, int col,
     cn = node_index(p, x, y, z);
     float t = 0.0f;
     for (int i = 0; i < 7; ++i) t += snap[(19 + i) * p.N + cn];
-    return p.Tm + t;
+    return p.Ts + t;
 }
 
 // The slopes s_p, s_q of column c' read the fronts of its neighbours (with a
@@ -447,8 +447,8 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                 for (int i = 0; i < 7; ++i) Th += gL[i];
 #pragma unroll
                 for (int i = 0; i < 19; ++i) { jx += ex(i) * fL[i]; jy += ey(i) * fL[i]; jz += ez(i) * fL[i]; }
-                const float TL = Th + p.Tm;
-                const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
+                const float TL = Th + p.Ts;
+                const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * (Th - p.dTms);
                 constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
                 constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
                 const float Nl1 = lgp[1] - lgp[2], Nl2 = lgp[3] - lgp[4], Nl3 = lgp[5] - lgp[6];
@@ -476,7 +476,7 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                     __fsub_rn(-__fadd_rn(__fadd_rn(__fmul_rn(mu[1], ux), __fmul_rn(mu[2], uy)), __fmul_rn(mu[3], uz)),
                               __fmul_rn(0.75f, mu[4])),
                     __fmul_rn(__fmul_rn(0.5f, p.gbeta), luz));
-                lgb[col] = __dadd_rn(lgb[col], __dmul_rn(0.5 * (double)Th, (double)luz));
+                lgb[col] = __dadd_rn(lgb[col], __dmul_rn(0.5 * (double)(Th - p.dTms), (double)luz));
                 float og[7];
 #pragma unroll
                 for (int i = 0; i < 7; ++i) og[i] = lTh;

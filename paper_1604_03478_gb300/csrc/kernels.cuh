@@ -62,10 +62,10 @@ __device__ __forceinline__ ST *elem(ST *base, IX c, long long off) {
 
 // Post-collision shifted g of a solid node: the ghost node (first solid node
 // of its column) takes the populations prepared by k_front; deeper nodes are
-// at rest at Tm, i.e. zero.
+// at rest at Tm (gh = w (Tm - Ts), zero with FP32 storage).
 __device__ __forceinline__ void solid_post(const KP &p, bool ghost, const float *gpost, int col, float (&g)[7]) {
 #pragma unroll
-    for (int i = 0; i < 7; ++i) g[i] = ghost ? __ldg(gpost + (long long)i * p.ncols + col) : 0.0f;
+    for (int i = 0; i < 7; ++i) g[i] = ghost ? __ldg(gpost + (long long)i * p.ncols + col) : w7(i) * p.dTms;
 }
 
 // A solid node at least two nodes above its column's first solid node and
@@ -164,11 +164,11 @@ __device__ __forceinline__ unsigned inside_mask(const KP &p, int x, int y, int z
 
 // Wall rule for a D3Q7 population leaving along link direction `dir`
 // across a wall: adiabatic bounce-back keeps it, the isothermal walls return
-// -v + 2 w (Tw - Tm) (anti-bounce-back, shifted populations).
+// -v + 2 w (Tw - Ts) (anti-bounce-back, shifted populations).
 template <int FACE>
 __device__ __forceinline__ float wall_value(const KP &p, int dir, float v, float Th_col) {
     const int w = wall_of_link<FACE>(dir);
-    return w == 3 ? v : -v + 2.0f * w7(dir) * ((w == 1 ? Th_col : p.Tc) - p.Tm);
+    return w == 3 ? v : -v + 2.0f * w7(dir) * ((w == 1 ? Th_col : p.Tc) - p.Ts);
 }
 
 // Across an x wall (x = 0 for e_x = +1 upstream, x = nx - 1 for e_x = -1):
@@ -306,7 +306,7 @@ __device__ __forceinline__ void gather_g(const KP &p, const ST *G, int x, int y,
             const int w = wall_of_link<FACE>(opp7(i));
             const float own = Store<ST>::ld(G + i * p.ld + c);
             g[i] = (w == 3) ? own
-                            : -own + 2.0f * w7(i) * ((w == 1 ? thw[column<FACE>(p, x, y, z)] : p.Tc) - p.Tm);
+                            : -own + 2.0f * w7(i) * ((w == 1 ? thw[column<FACE>(p, x, y, z)] : p.Tc) - p.Ts);
         }
     }
 }
@@ -358,13 +358,13 @@ __device__ __forceinline__ void gather_f9(const KP &p, const ST *F, const int (&
     }
 }
 
-// Tm + the sum of the shifted g (the temperature the front reads; FP32, the
+// Ts + the sum of the shifted g (the temperature the front reads; FP32, the
 // precision the populations are held in).
 __device__ __forceinline__ float sum_T(const KP &p, const float (&g)[7]) {
     float t = 0.0f;
 #pragma unroll
     for (int i = 0; i < 7; ++i) t += g[i];
-    return p.Tm + t;
+    return p.Ts + t;
 }
 
 template <typename ST, int FACE>
@@ -496,7 +496,7 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     // ghost temperature plus the non-equilibrium part N^-1 (I - Q)(n - n^eq)
     // of the post-collision populations of the liquid node below
     float gh[7];
-    const float dTg = Tg - Tm;
+    const float dTg = Tg - p.Ts;
 #pragma unroll
     for (int i = 0; i < 7; ++i) gh[i] = w7(i) * dTg;
     if (jn >= 1) {
@@ -521,8 +521,8 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
             jy += ey(i) * fL[i];
             jz += ez(i) * fL[i];
         }
-        const float TL = Th + p.Tm;
-        const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * Th;
+        const float TL = Th + p.Ts;
+        const float ux = jx, uy = jy, uz = jz + 0.5f * p.gbeta * (Th - p.dTms);
         constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
         constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
         const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
@@ -662,8 +662,8 @@ __global__ void __launch_bounds__(128) k_macro(const __grid_constant__ KP p, con
         for (int i = 0; i < 7; ++i) Th += g[i];
 #pragma unroll
         for (int i = 0; i < 19; ++i) { ux += ex(i) * f[i]; uy += ey(i) * f[i]; uz += ez(i) * f[i]; }
-        uz += 0.5f * p.gbeta * Th;
-        Tc = p.Tm + Th;
+        uz += 0.5f * p.gbeta * (Th - p.dTms);
+        Tc = p.Ts + Th;
     }
     if (T) T[c] = Tc;
     if (u) { u[3 * c] = ux; u[3 * c + 1] = uy; u[3 * c + 2] = uz; }
@@ -687,12 +687,12 @@ __global__ void __launch_bounds__(128) k_state_out(const __grid_constant__ KP p,
         float g[7];
         if (a >= js[col] && deep_solid(p, a, nb[col])) {
 #pragma unroll
-            for (int i = 0; i < 7; ++i) g[i] = 0.0f;
+            for (int i = 0; i < 7; ++i) g[i] = w7(i) * p.dTms;
         } else {
             gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
         }
 #pragma unroll
-        for (int i = 0; i < 7; ++i) go[i * p.N + c] = g[i] + w7(i) * p.Tm;
+        for (int i = 0; i < 7; ++i) go[i * p.N + c] = g[i] + w7(i) * p.Ts;
     }
     if (fo) {
         float f[19];
@@ -720,7 +720,8 @@ __global__ void __launch_bounds__(128) k_state_in(const __grid_constant__ KP p, 
     const bool liq = a < js[col];
     if (gi)
 #pragma unroll
-        for (int i = 0; i < 7; ++i) Store<ST>::st(G + i * p.ld + c, liq ? gi[i * p.N + c] - w7(i) * p.Tm : 0.0f);
+        for (int i = 0; i < 7; ++i)
+            Store<ST>::st(G + i * p.ld + c, liq ? gi[i * p.N + c] - w7(i) * p.Ts : w7(i) * p.dTms);
     if (fi)
 #pragma unroll
         for (int i = 0; i < 19; ++i) Store<ST>::st(F + i * p.ld + c, liq ? fi[i * p.N + c] - w19(i) : 0.0f);
@@ -737,7 +738,7 @@ __global__ void __launch_bounds__(128) k_init(const __grid_constant__ KP p, ST *
     if (x >= p.nx || y >= p.ny) return;
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
-    const float dT = a < js[col] ? Tprof[a] - p.Tm : 0.0f;
+    const float dT = a < js[col] ? Tprof[a] - p.Ts : p.dTms;
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store<ST>::st(F + i * p.ld + c, 0.0f);
 #pragma unroll
@@ -764,7 +765,7 @@ __global__ void __launch_bounds__(128) k_nusselt(const __grid_constant__ KP p, c
     column_node<FACE>(p, col, 0, x, y, z);
     constexpr int up = FACE == 0 ? 3 : 5;  // the D3Q7 direction leaving the heated wall
     const double v = (double)Store<ST>::ld(G + up * p.ld + node_index(p, x, y, z));
-    const double wt = (double)w7(up) * ((double)thw[col] - p.Tm_d);
+    const double wt = (double)w7(up) * ((double)thw[col] - (double)p.Ts);
     nu[col] = (inflight ? 2.0 * (wt - v) : 2.0 * (v - wt)) * scale;
 }
 
@@ -789,8 +790,8 @@ __global__ void __launch_bounds__(256) k_totals_part(const __grid_constant__ KP 
         for (int i = 0; i < 7; ++i) Th += g[i];
 #pragma unroll
         for (int i = 0; i < 19; ++i) { rh += f[i]; ux += ex(i) * f[i]; uy += ey(i) * f[i]; uz += ez(i) * f[i]; }
-        uz += 0.5f * p.gbeta * Th;
-        sT += Th;
+        uz += 0.5f * p.gbeta * (Th - p.dTms);
+        sT += Th - p.dTms;
         sr += rh;
         n += 1.0;
         const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;

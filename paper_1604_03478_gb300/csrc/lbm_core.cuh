@@ -1,10 +1,13 @@
 // lbm_core.cuh -- lattice constants, kernel parameters and the per-node
 // double-MRT collision (Li, Yang & Zhang, arXiv:1604.03478, Eqs. 1-5).
 //
-// Storage convention: every distribution is held SHIFTED by its rest
-// equilibrium, fh_i = f_i - w_i rho0 (rho0 = 1) and gh_i = g_i - w_i Tm, so
-// that a liquid node at rest and a solid node at Tm are all zeros and the
-// stored numbers are small (FP16 storage keeps its precision for them).
+// Storage convention: every distribution is held SHIFTED by a rest
+// equilibrium, fh_i = f_i - w_i rho0 (rho0 = 1) and gh_i = g_i - w_i Ts, so
+// that the stored numbers are small (FP16 storage keeps its precision for
+// them).  Ts is Tm with FP32 storage (a liquid node at rest and a solid node
+// at Tm are all zeros) and the mid temperature (Th + Tm) / 2 with FP16
+// storage, which halves the largest stored energy population (|T - Ts| <=
+// (Th - Tm) / 2 instead of Th - Tm).
 // Arrays are direction-major: direction i of node c lives at base[i*ld + c].
 #pragma once
 
@@ -105,6 +108,8 @@ struct KP {
     long long N;      // nodes
     long long ld;     // distance between direction arrays (elements)
     float Tm, Tc, gbeta;
+    float Ts;         // storage shift of g: gh = g - w Ts
+    float dTms;       // Tm - Ts: a node at rest at Tm holds gh = w dTms
     float s_e, s_eps, s_q, s_nu, s_pi, s_m;
     float s_alpha, s_g4, s_g5;
     double Tm_d, Th_d;
@@ -367,7 +372,7 @@ __host__ __device__ __forceinline__ void add_back_shared(float (&f)[19], const f
 
 // -------------------------------------------------------------- collision
 // One liquid node: shifted populations in, shifted post-collision out.
-//   T = Tm + sum gh;  F = g beta (T - Tm) z-hat (Boussinesq, gravity -z);
+//   T = Ts + sum gh;  F = g beta (T - Tm) z-hat (Boussinesq, gravity -z);
 //   u = sum fh e + F/2 (rho0 = 1);
 //   D3Q19 (Eq. 2 with the Guo source): m* - m = -S (m - m^eq) + (I - S/2) M F~,
 //   f* = f + M^T D^-1 (m* - m);
@@ -377,8 +382,8 @@ __host__ __device__ __forceinline__ void add_back_shared(float (&f)[19], const f
 // Guo's source for a force along z.  Writes u (for diagnostics) to uout.
 __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[7], float *uout = nullptr) {
     float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-    const float T = Th + p.Tm;
-    const float Fz = p.gbeta * Th;
+    const float T = Th + p.Ts;
+    const float Fz = p.gbeta * (Th - p.dTms);  // g beta (T - Tm)
     float m[19], S[9], D[9];
 #pragma unroll
     for (int P = 0; P < 9; ++P) {

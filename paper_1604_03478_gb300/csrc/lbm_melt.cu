@@ -461,6 +461,10 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     p.s_pi = (float)d.s_pi; p.s_m = (float)d.s_m;
     p.s_alpha = (float)d.s_alpha; p.s_g4 = (float)d.s_g4; p.s_g5 = (float)d.s_g5;
     p.Tm_d = Tm; p.Th_d = Th;
+    // storage shift of the energy populations: Tm, or the mid temperature
+    // for FP16 storage (halves the largest stored value)
+    p.Ts = h->precision == 1 ? (float)(0.5 * (Th + Tm)) : (float)Tm;
+    p.dTms = (float)Tm - p.Ts;
     p.coef = Ste > 0.0 ? d.alpha * Ste / (Th - Tm) : 0.0;
     p.coef_f = (float)p.coef;
     p.skip_deep = (Tc == Tm) ? 1 : 0;
