@@ -197,7 +197,8 @@ def test_hot_wall_field(lib, orc, when):
 
 def test_fp16_storage_error(lib, orc):
     """Shifted-FP16 storage, FP32 arithmetic: the error against the FP64
-    oracle is reported, and bounded well below the flow's own scales."""
+    oracle is reported, and bounded well below the flow's own scales (1.8e-4
+    measured with g shifted by the mid temperature; 5e-4 here)."""
     kw = dict(face=0, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True)
     gpu = lib(24, 20, 16, precision=1, **kw)
     o = orc.Oracle(24, 20, 16, **kw)
@@ -207,7 +208,7 @@ def test_fp16_storage_error(lib, orc):
     To, uo, So, lfo = o.get()
     dT, dlf = np.abs(Tg - To).max(), abs(lfg - lfo)
     print("fp16 storage: max|dT| = %.3g, |dlf| = %.3g" % (dT, dlf))
-    assert dT < 2e-2 and dlf < 2e-3
+    assert dT < 5e-4 and dlf < 1e-5
 
 
 def test_totals_and_report(lib, orc):
