@@ -79,12 +79,11 @@ def reduce_across_ranks(ms, units, dist=None, device="cpu"):
     return float(t.item()), float(u.item())
 
 
-# Sources of the stream-collide launch (kernels, their launchers and the step
-# loop that sizes the grid): a recorded DRAM traffic figure holds only while
-# they are unchanged.
+# Sources of the stream-collide kernels and their launchers: a recorded DRAM
+# traffic figure holds only while they are unchanged.
 K1_SOURCES = ("paper_1604_03478_gb300/csrc/kernels.cuh", "paper_1604_03478_gb300/csrc/lbm_core.cuh",
               "paper_1604_03478_gb300/csrc/launch.h", "paper_1604_03478_gb300/csrc/launch_impl.cuh",
-              "paper_1604_03478_gb300/csrc/k_f32.cu", "paper_1604_03478_gb300/csrc/lbm_melt.cu")
+              "paper_1604_03478_gb300/csrc/k_f32.cu")
 TRAFFIC_RECORD = "profiles/stream_collide_256cube_fp32_traffic.md"
 
 
