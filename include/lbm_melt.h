@@ -272,8 +272,10 @@ void lbm_melt_destroy(lbm_melt *h);
    front status of the handle is flagged: the reverse sweep relies on fronts
    that moved at most half a node per step; and LBM_EINVAL when the
    heated-wall field was set after the recorded run (the sweep recomputes
-   the run with it).  The recomputed segments of full length are captured
-   into CUDA graphs once and replayed. */
+   the run with it).  The recomputation of a segment and the reverse sweep
+   of the segment after it run concurrently on the handle's stream and an
+   internal one (two snapshot sets when the device has room for them; full
+   segments replayed from CUDA graphs). */
 lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every);
 lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed_dL_dS, double *dL_dTh, double *dL_dparams,
                                   int ptr_kind);

@@ -782,17 +782,20 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     const dim3 grd = lbm::node_grid_axial(p, blk, h->face, abound);
     const int cb = h->cblk;
     const dim3 cgrid = lbm::col_grid((long long)nc, cb);
-    // buffers
+    // buffers; the snapshots of a segment twice, so that one segment's
+    // recomputation fills one set while the previous segment's reverse sweep
+    // reads the other
     unsigned char *fin = nullptr;
-    float *snap = nullptr, *lam[2] = {nullptr, nullptr}, *lgpost = nullptr;
-    double *snap_s = nullptr, *lams[2] = {nullptr, nullptr}, *wp[2] = {nullptr, nullptr}, *wq[2] = {nullptr, nullptr};
+    float *snapb[2] = {nullptr, nullptr}, *lam[2] = {nullptr, nullptr}, *lgpost = nullptr;
+    double *snap_sb[2] = {nullptr, nullptr}, *lams[2] = {nullptr, nullptr}, *wp[2] = {nullptr, nullptr},
+           *wq[2] = {nullptr, nullptr};
     double *lthw = nullptr;
     double *part = nullptr, *lsal = nullptr, *lgb = nullptr, *lcoef = nullptr, *acc = nullptr;
-    int *snap_js = nullptr, *snap_nb = nullptr;
+    int *snap_jsb[2] = {nullptr, nullptr}, *snap_nbb[2] = {nullptr, nullptr};
     struct Alloc { void **p; size_t b; } al[] = {
-        {(void **)&fin, t->ck_bytes}, {(void **)&snap, (size_t)(C + 1) * 26 * N * 4},
-        {(void **)&snap_s, (size_t)(C + 1) * nc * 8}, {(void **)&snap_js, (size_t)(C + 1) * nc * 4},
-        {(void **)&snap_nb, (size_t)(C + 1) * nc * 4},
+        {(void **)&fin, t->ck_bytes}, {(void **)&snapb[0], (size_t)(C + 1) * 26 * N * 4},
+        {(void **)&snap_sb[0], (size_t)(C + 1) * nc * 8}, {(void **)&snap_jsb[0], (size_t)(C + 1) * nc * 4},
+        {(void **)&snap_nbb[0], (size_t)(C + 1) * nc * 4},
         {(void **)&lam[0], 26 * N * 4}, {(void **)&lam[1], 26 * N * 4}, {(void **)&lgpost, 7 * nc * 4},
         {(void **)&lams[0], nc * 8}, {(void **)&lams[1], nc * 8}, {(void **)&wp[0], nc * 8}, {(void **)&wq[0], nc * 8},
         {(void **)&wp[1], nc * 8}, {(void **)&wq[1], nc * 8},
@@ -801,6 +804,10 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     lbm_status st = LBM_OK;
     auto cleanup = [&]() {
         for (auto &a : al) cudaFree(*a.p);
+        cudaFree(snapb[1]);
+        cudaFree(snap_sb[1]);
+        cudaFree(snap_jsb[1]);
+        cudaFree(snap_nbb[1]);
     };
     for (auto &a : al) {
         cudaError_t e = cudaMalloc(a.p, a.b);
@@ -808,6 +815,16 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             cleanup();
             return tape_err(h, LBM_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
         }
+    }
+    // the second snapshot set if the device has room for it (else the
+    // segments run one after another through the first)
+    int nsets = 2;
+    if (cudaMalloc(&snapb[1], (size_t)(C + 1) * 26 * N * 4) != cudaSuccess ||
+        cudaMalloc(&snap_sb[1], (size_t)(C + 1) * nc * 8) != cudaSuccess ||
+        cudaMalloc(&snap_jsb[1], (size_t)(C + 1) * nc * 4) != cudaSuccess ||
+        cudaMalloc(&snap_nbb[1], (size_t)(C + 1) * nc * 4) != cudaSuccess) {
+        (void)cudaGetLastError();
+        nsets = 1;
     }
 #define BCK(call, where)                                                             \
     do {                                                                             \
@@ -822,17 +839,24 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
     const long long fin_steps = h->steps;
     if ((st = move_state(h, fin, 0)) != LBM_OK) { cleanup(); return st; }
     for (auto &a : al)
-        if (a.p != (void **)&fin && a.p != (void **)&snap) BCK(cudaMemsetAsync(*a.p, 0, a.b, h->stream), "zero");
+        if (a.p != (void **)&fin && a.p != (void **)&snapb[0] && a.p != (void **)&snapb[1])
+            BCK(cudaMemsetAsync(*a.p, 0, a.b, h->stream), "zero");
+    if (nsets == 2) {
+        BCK(cudaMemsetAsync(snap_sb[1], 0, (size_t)(C + 1) * nc * 8, h->stream), "zero");
+        BCK(cudaMemsetAsync(snap_jsb[1], 0, (size_t)(C + 1) * nc * 4, h->stream), "zero");
+        BCK(cudaMemsetAsync(snap_nbb[1], 0, (size_t)(C + 1) * nc * 4, h->stream), "zero");
+    }
     BCK(cudaMemcpyAsync(lams[1], seed, nc * 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         h->stream), "seed");
-    // One segment: snapshot of its first level, the recomputed steps with a
-    // snapshot after each, then the reverse sweep over its levels.  All of
-    // it goes on stream sm (so that it can be captured into a graph), from
-    // phase (cur, inflight), with the stream-collide grids cut at the run's
-    // height bound; the adjoint buffers alternate as the levels go by.
+    // A segment's recomputation: snapshot of its first level, then the
+    // recomputed steps with a snapshot after each, into snapshot set b, on
+    // stream sm from phase (cur, inflight), the stream-collide grids cut at
+    // the run's height bound.  It reads and writes the handle's state.
     const float *thw = h->thw_cur;
-    auto enqueue_segment = [&](long long len, int cur, int inflight, cudaStream_t sm, float *(&lm)[2],
-                               double *(&lms)[2]) -> cudaError_t {
+    auto enqueue_recompute = [&](long long len, int cur, int inflight, int b, cudaStream_t sm) -> cudaError_t {
+        float *snap = snapb[b];
+        double *snap_s = snap_sb[b];
+        int *snap_js = snap_jsb[b], *snap_nb = snap_nbb[b];
         auto snapshot = [&](long long j) {
             float *out = snap + (size_t)j * 26 * N;
             double *os = snap_s + (size_t)j * nc;
@@ -855,6 +879,16 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             e = lbm_enqueue_step(h, cur, inflight, abound, sm);
             if (e == cudaSuccess) e = snapshot(j);
         }
+        return e;
+    };
+    // A segment's reverse sweep over its levels from snapshot set b, on
+    // stream sm; it reads only the snapshots and the adjoint buffers, which
+    // alternate as the levels go by.
+    auto enqueue_reverse = [&](long long len, int b, cudaStream_t sm, float *(&lm)[2], double *(&lms)[2]) -> cudaError_t {
+        const float *snap = snapb[b];
+        const double *snap_s = snap_sb[b];
+        const int *snap_js = snap_jsb[b], *snap_nb = snap_nbb[b];
+        cudaError_t e = cudaSuccess;
         for (long long j = len - 1; j >= 0 && e == cudaSuccess; --j) {
             const float *s1 = snap + (size_t)(j + 1) * 26 * N, *s0 = snap + (size_t)j * 26 * N;
             const double *st_s = snap_s + (size_t)j * nc;
@@ -889,52 +923,108 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         }
         return e;
     };
-    // Full-length segments all run the same launches from the same phase
-    // (and the same parity of the alternating buffers), so each such
+    // The recomputation of a segment (stream A: the handle's stream, which
+    // owns the state) and the reverse sweep of the segment after it (stream
+    // B) do not share data, so they run at the same time on the two snapshot
+    // sets; events order each set's writer after its previous reader.
+    // Full-length segments run the same launches from the same phase (and
+    // the same parity of the alternating adjoint buffers), so each
     // combination is captured into a CUDA graph once and replayed: the
     // host's launches would otherwise bound small cavities.
-    struct SegGraph { int cur, inflight, par; cudaGraphExec_t exec; };
+    struct SegGraph { int kind, a, b, c; cudaGraphExec_t exec; };
     std::vector<SegGraph> seg_graphs;
     float *const lam0_first = lam[0];
+    cudaStream_t sB = nullptr;
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr}, ev_set = nullptr;
     auto free_graphs = [&]() {
         for (auto &g : seg_graphs) cudaGraphExecDestroy(g.exec);
         seg_graphs.clear();
+        for (int i = 0; i < 2; ++i) {
+            if (ev_rec[i]) cudaEventDestroy(ev_rec[i]);
+            if (ev_rev[i]) cudaEventDestroy(ev_rev[i]);
+        }
+        if (ev_set) cudaEventDestroy(ev_set);
+        if (sB) cudaStreamDestroy(sB);
     };
     if (!h->cap_stream) BCK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    BCK(cudaStreamCreateWithFlags(&sB, cudaStreamNonBlocking), "reverse stream");
+    for (int i = 0; i < 2; ++i) {
+        BCK(cudaEventCreateWithFlags(&ev_rec[i], cudaEventDisableTiming), "event");
+        BCK(cudaEventCreateWithFlags(&ev_rev[i], cudaEventDisableTiming), "event");
+    }
+    BCK(cudaEventCreateWithFlags(&ev_set, cudaEventDisableTiming), "event");
+    // the reverse stream starts after the zeroed buffers and the seed
+    BCK(cudaEventRecord(ev_set, h->stream), "event");
+    BCK(cudaStreamWaitEvent(sB, ev_set, 0), "wait");
+    // a cached graph for (kind, a, b, c), else capture it from enqueue()
+    auto graph_of = [&](int kind, int a, int b, int c, const auto &enqueue, cudaGraphExec_t *out) -> cudaError_t {
+        for (auto &g : seg_graphs)
+            if (g.kind == kind && g.a == a && g.b == b && g.c == c) { *out = g.exec; return cudaSuccess; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = enqueue(h->cap_stream);
+            const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) seg_graphs.push_back({kind, a, b, c, *out});
+        return e;
+    };
+    bool used[2] = {false, false};
     for (long long sgm = t->nseg - 1; sgm >= 0 && st == LBM_OK; --sgm) {
         const long long len = std::min(C, t->T - sgm * C);
-        if ((st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
+        const int b = nsets == 2 ? (int)(sgm & 1) : 0;
+        const bool full = len == C && t->nseg > 2;
+        cudaError_t e = cudaSuccess;
+        // stream A: the set's previous reader done, restore the checkpoint,
+        // recompute into the set
+        if (used[b]) e = cudaStreamWaitEvent(h->stream, ev_rev[b], 0);
+        if (e == cudaSuccess && (st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
         const int cur0 = t->ck_cur[sgm], infl0 = t->ck_inflight[sgm];
         h->steps = t->ck_steps[sgm];
-        cudaError_t e = cudaSuccess;
-        if (len == C && t->nseg > 2) {
-            const int par = lam[0] == lam0_first ? 0 : 1;
-            cudaGraphExec_t exec = nullptr;
-            for (auto &g : seg_graphs)
-                if (g.cur == cur0 && g.inflight == infl0 && g.par == par) exec = g.exec;
-            if (!exec) {
-                float *lm[2] = {lam[0], lam[1]};
-                double *lms[2] = {lams[0], lams[1]};
-                cudaGraph_t graph = nullptr;
-                e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    e = enqueue_segment(len, cur0, infl0, h->cap_stream, lm, lms);
-                    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                if (e == cudaSuccess) seg_graphs.push_back({cur0, infl0, par, exec});
+        if (e == cudaSuccess) {
+            if (full) {
+                cudaGraphExec_t exec = nullptr;
+                e = graph_of(0, cur0, infl0, b,
+                             [&](cudaStream_t sm) { return enqueue_recompute(len, cur0, infl0, b, sm); }, &exec);
+                if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+            } else {
+                e = enqueue_recompute(len, cur0, infl0, b, h->stream);
             }
-            if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
-            if (len & 1) {
-                std::swap(lam[0], lam[1]);
-                std::swap(lams[0], lams[1]);
-            }
-        } else {
-            e = enqueue_segment(len, cur0, infl0, h->stream, lam, lams);
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_rec[b], h->stream);
+        // stream B: reverse the segment once its snapshots are in
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sB, ev_rec[b], 0);
+        if (e == cudaSuccess) {
+            if (full) {
+                const int par = lam[0] == lam0_first ? 0 : 1;
+                cudaGraphExec_t exec = nullptr;
+                e = graph_of(1, par, b, 0,
+                             [&](cudaStream_t sm) {
+                                 float *lm[2] = {lam[0], lam[1]};
+                                 double *lms[2] = {lams[0], lams[1]};
+                                 return enqueue_reverse(len, b, sm, lm, lms);
+                             }, &exec);
+                if (e == cudaSuccess) e = cudaGraphLaunch(exec, sB);
+                if (len & 1) {
+                    std::swap(lam[0], lam[1]);
+                    std::swap(lams[0], lams[1]);
+                }
+            } else {
+                e = enqueue_reverse(len, b, sB, lam, lams);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_rev[b], sB);
+        used[b] = true;
         if (e != cudaSuccess) st = tape_err(h, LBM_ECUDA, "adjoint segment: %s", cudaGetErrorString(e));
+    }
+    // the sums below run on stream A after the last reverse sweep
+    if (st == LBM_OK) {
+        cudaError_t e = cudaEventRecord(ev_set, sB);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev_set, 0);
+        if (e != cudaSuccess) st = tape_err(h, LBM_ECUDA, "adjoint join: %s", cudaGetErrorString(e));
     }
     if (st == LBM_OK) {
         // parameter sensitivities: acc = {d/ds_nu, d/ds_alpha, d/dcoef, d/dgbeta}
@@ -974,7 +1064,8 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
             }
         }
     }
-    // restore the final state
+    // restore the final state (after everything on both streams)
+    if (sB) cudaStreamSynchronize(sB);
     lbm_status st2 = move_state(h, fin, 1);
     h->cur = fin_cur;
     h->inflight = fin_inflight;
