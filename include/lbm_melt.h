@@ -299,10 +299,11 @@ typedef struct {
     lbm_melt_rates rates;
 } lbm_melt_case;
 
-/* Create n cavities (all with the same storage precision) on the current
-   device.  The ensemble runs on a stream of its own, ordered after the work
-   queued on cuda_stream at each call and before the work queued there
-   afterwards. */
+/* Create n cavities (all with the same storage precision, n <= 64, each
+   with fewer than 2^32 / 19 stored elements per direction array, about
+   2.2e8 nodes) on the current device; LBM_EINVAL otherwise.  The ensemble
+   runs on a stream of its own, ordered after the work queued on cuda_stream
+   at each call and before the work queued there afterwards. */
 lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *cuda_stream, lbm_ensemble **out);
 
 /* Advance every member by nsteps steps.  Asynchronous. */
