@@ -55,7 +55,8 @@ class _Cfg(C.Structure):
                 ("Tc", C.c_double), ("Tm", C.c_double), ("Ma", C.c_double), ("s0", C.c_double),
                 ("s_nu", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
                 ("s_pi", C.c_double), ("s_m", C.c_double), ("s_alpha", C.c_double),
-                ("s_g4", C.c_double), ("s_g5", C.c_double), ("derive", C.c_int)]
+                ("s_g4", C.c_double), ("s_g5", C.c_double), ("derive", C.c_int),
+                ("solid", C.c_int), ("ks_kl", C.c_double)]
 
 
 _lib = None
@@ -110,6 +111,12 @@ def lib() -> C.CDLL:
         L.orc_front_gradient.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double]
         L.orc_ghost_T.restype = C.c_double
         L.orc_ghost_T.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double]
+        L.orc_solid_gradient.restype = C.c_double
+        L.orc_solid_gradient.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double]
+        L.orc_solid_ghost_T.restype = C.c_double
+        L.orc_solid_ghost_T.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_double]
+        L.orc_neumann_lambda2.restype = C.c_double
+        L.orc_neumann_lambda2.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_lattice19.argtypes = [ip, ip, ip, dp, ip]
         L.orc_lattice7.argtypes = [ip, ip, ip, dp, ip]
         L.orc_matrices.argtypes = [dp, dp, dp, dp]
@@ -198,6 +205,22 @@ def ghost_T(Tcol, s, Tw, Tm):
     return lib().orc_ghost_T(_p(Tcol), len(Tcol), float(s), float(Tw), float(Tm))
 
 
+def solid_gradient(Tcol, s, Tc, Tm):
+    Tcol = np.ascontiguousarray(Tcol, float)
+    return lib().orc_solid_gradient(_p(Tcol), len(Tcol), float(s), float(Tc), float(Tm))
+
+
+def solid_ghost_T(Tcol, s, Tc, Tm):
+    Tcol = np.ascontiguousarray(Tcol, float)
+    return lib().orc_solid_ghost_T(_p(Tcol), len(Tcol), float(s), float(Tc), float(Tm))
+
+
+def neumann_lambda2(Ste, theta, kappa):
+    """Two-phase Neumann front constant: s = 2 lambda sqrt(alpha_l t) for a
+    solid initially at Tc, theta = (Tm - Tc) / (Th - Tm), kappa = k_s / k_l."""
+    return lib().orc_neumann_lambda2(float(Ste), float(theta), float(kappa))
+
+
 def num_threads():
     return lib().orc_num_threads()
 
@@ -210,7 +233,7 @@ def set_num_threads(n):
 # ---------------------------------------------------------------- simulator
 
 INFO_KEYS = ("nu", "alpha", "gbeta", "lambda", "t0", "s_nu", "s_alpha", "H", "steps",
-             "q_hot", "q_cold", "mass", "n_liquid", "sum_T_liquid")
+             "q_hot", "q_cold", "mass", "n_liquid", "sum_T_liquid", "sum_T_solid", "alpha_s")
 
 
 class OracleError(RuntimeError):
@@ -223,16 +246,20 @@ class Oracle:
     Arguments mirror the library's create call: grid (nx, ny, nz), heated face
     (0: y = 0, 1: z = 0), Ra, Pr, Ste, Th, Tc, Tm, Ma, initial front s0, and
     the relaxation rates.  With ``derive`` the rates s_nu and s_alpha follow
-    from Ra, Pr, Ma and H; otherwise pass them explicitly.
+    from Ra, Pr, Ma and H; otherwise pass them explicitly.  ``solid`` = 1
+    turns on heat conduction in the solid (conductivity ratio ``ks_kl`` =
+    k_s / k_l), the k_s term of Eq. 6.
     """
 
     def __init__(self, nx, ny, nz, face=0, Ra=0.0, Pr=1.0, Ste=0.1, Th=1.0, Tc=0.0, Tm=0.0,
-                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, _lib=None, **rates):
+                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, solid=0, ks_kl=1.0, _lib=None,
+                 **rates):
         self._L = _lib if _lib is not None else lib()
         r = dict(DEFAULT_RATES)
         r.update(rates)
         cfg = _Cfg(nx, ny, nz, face, Ra, Pr, Ste, Th, Tc, Tm, Ma, s0, s_nu, r["s_e"], r["s_eps"],
-                   r["s_q"], r["s_pi"], r["s_m"], s_alpha, r["s_g4"], r["s_g5"], 1 if derive else 0)
+                   r["s_q"], r["s_pi"], r["s_m"], s_alpha, r["s_g4"], r["s_g5"], 1 if derive else 0,
+                   int(solid), float(ks_kl))
         err = C.create_string_buffer(256)
         h = self._L.orc_create(C.byref(cfg), err, 256)
         if not h:

@@ -55,6 +55,29 @@
  *     unchanged (every node, solid or liquid, holds and streams g).
  *   - The initial front sits at s0 (one lattice unit by default) with the
  *     liquid at the analytic conduction (Neumann) temperature of that front.
+ *
+ * Solid-phase conduction (cfg.solid = 1; the paper solves only Tc = Tm,
+ * where the solid stays at Tm and the k_s term of Eq. 6 vanishes):
+ *   - rho_s c_s = rho_l c_l, so the solid diffusivity is alpha_s =
+ *     (k_s / k_l) alpha; a solid node runs the D3Q7 MRT collision at u = 0
+ *     with that diffusivity, and its populations stream among solid nodes
+ *     and against the walls like the liquid's.
+ *   - The interface is imposed on each side by the mirror of the liquid-side
+ *     ghost rule: the last liquid node of a column is the solid side's ghost,
+ *     with the temperature extrapolated through (s, Tm) and the lowest solid
+ *     node at least half a cell above s (the cold wall (H, Tc) standing in
+ *     for a missing one), plus the non-equilibrium part of the solid node
+ *     above it.  A population that crosses the phase boundary from a node
+ *     of the other phase is that node's ghost population when the node is
+ *     its column's ghost for the receiving phase, else the rest state at Tm.
+ *   - Eq. 6 gains k_s dT_s/dy: the solid-side gradient at s is the one-sided
+ *     quadratic through (s, Tm) and the two lowest solid nodes at least half
+ *     a cell above s (the cold wall standing in for a missing one), linear
+ *     through (s, Tm) and (H, Tc) when none qualifies, and zero in a column
+ *     with no solid node.
+ *   - The initial solid is at the two-phase Neumann temperature of the front
+ *     s0 (a solid initially at Tc); with Tc = Tm everything reduces to the
+ *     method above.
  */
 #include <math.h>
 #include <stdio.h>
@@ -107,6 +130,8 @@ typedef struct orc_cfg {
     double s_nu, s_e, s_eps, s_q, s_pi, s_m;
     double s_alpha, s_g4, s_g5;
     int derive; /* 1: s_nu and s_alpha from Ra, Pr, Ma and H; 0: as given */
+    int solid;    /* 0: solid held at Tm (zero subcooling); 1: heat conduction in the solid */
+    double ks_kl; /* k_s / k_l, the solid's conductivity ratio (solid = 1) */
 } orc_cfg;
 
 typedef struct orc_sim {
@@ -118,9 +143,11 @@ typedef struct orc_sim {
     double lambda, t0, Ra_im;
     double M[Q19 * Q19], Minv[Q19 * Q19], Nm[Q7 * Q7], Ninv[Q7 * Q7];
     real S[Q19], Qr[Q7];
+    real alpha_s, Qs[Q7];       /* solid diffusivity and D3Q7 rates (solid = 1) */
     real *f, *g, *fs, *gs;     /* current (post-streaming) and post-collision */
     real *s, *snew, *Tghost, *Thw;
     real *Gpost;                /* ghost-node post-collision g, 7 per column */
+    real *Spost;                /* solid-side ghost post-collision g, 7 per column (solid = 1) */
     int *js;                      /* number of liquid nodes per column */
     unsigned char *liq;
     long steps;
@@ -327,6 +354,32 @@ double orc_neumann_lambda(double Ste) {
     return 0.5 * (lo + hi);
 }
 
+/* Two-phase Neumann solution of conduction melting (a solid initially at
+   Tc < Tm; conductivity ratio kappa = k_s / k_l and equal rho c in both
+   phases, so alpha_s = kappa alpha_l): the front is s = 2 lambda
+   sqrt(alpha_l t), and the interface energy balance (Eq. 6 in one dimension)
+   fixes lambda as the root of
+       lambda sqrt(pi) / Ste = exp(-lambda^2) / erf(lambda)
+           - theta sqrt(kappa) exp(-lambda^2 / kappa) / erfc(lambda / sqrt(kappa))
+   with theta = (Tm - Tc) / (Th - Tm).  The right side falls and the left
+   rises with lambda, so the root is unique; bisection.  theta = 0 gives the
+   one-phase equation of orc_neumann_lambda. */
+static double neumann2_residual(double l, double Ste, double theta, double kappa) {
+    double r = sqrt(kappa);
+    return l * sqrt(M_PI) / Ste - exp(-l * l) / erf(l) + theta * r * exp(-l * l / kappa) / erfc(l / r);
+}
+
+double orc_neumann_lambda2(double Ste, double theta, double kappa) {
+    if (!(Ste > 0.0) || !(kappa > 0.0)) return 0.0;
+    double lo = 0.0, hi = 1.0;
+    while (neumann2_residual(hi, Ste, theta, kappa) < 0.0) hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (neumann2_residual(mid, Ste, theta, kappa) < 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 /* Highest node k (centre k + 1/2) at least half a cell below s, or -1. */
 static int guarded_node(real s, int n) {
     int k = (int)floor(RE(s) - 1.0);
@@ -368,6 +421,42 @@ static real ghost_T(const real *Tcol, int n, real s, real Tw, real Tm) {
     int k = guarded_node(s, n);
     if (k < 0) return Tm + (Tm - Tw) * (yg - s) / s;
     return Tm + (Tm - Tcol[k]) * (yg - s) / (s - (k + 0.5));
+}
+
+/* Lowest node k (centre k + 1/2) at least half a cell above s, i.e. the
+   smallest k >= s; n when there is none. */
+static int guarded_solid_node(real s, int n) {
+    int k = (int)ceil(RE(s));
+    return k > n ? n : k;
+}
+
+/* Solid-side dT/da at the front a = s of one column (the k_s dT_s/dy term of
+   Eq. 6), the mirror of front_gradient: quadratic through (s, Tm) and the
+   guarded solid node k with the node above it, the cold wall (n, Tc)
+   standing in for node k + 1 = n; linear through (s, Tm) and (n, Tc) when no
+   node is at least half a cell above s.  The caller takes it only in a
+   column with a solid node (s <= n - 1/2).  Written with the deviations
+   from Tm, so that a solid at Tm gives exactly zero. */
+static real solid_gradient(const real *Tcol, int n, real s, real Tc, real Tm) {
+    int k = guarded_solid_node(s, n);
+    if (k >= n) return (Tc - Tm) / (n - s);
+    real x1 = k + 0.5, Y1 = Tcol[k] - Tm, x2, Y2;
+    if (k + 1 < n) { x2 = k + 1.5; Y2 = Tcol[k + 1] - Tm; }
+    else           { x2 = n;       Y2 = Tc - Tm; }
+    return Y1 * (s - x2) / ((x1 - s) * (x1 - x2)) + Y2 * (s - x1) / ((x2 - s) * (x2 - x1));
+}
+
+/* Ghost temperature of the solid side at the last liquid node of a column
+   (centre js - 1/2): the line through (s, Tm) and the guarded solid node (or
+   the cold wall), evaluated there.  Tm when the column has no liquid or no
+   solid node. */
+static real solid_ghost_T(const real *Tcol, int n, real s, real Tc, real Tm) {
+    int js = n_liquid(s, n);
+    if (js < 1 || js >= n) return Tm;
+    real yg = js - 0.5;
+    int k = guarded_solid_node(s, n);
+    if (k >= n) return Tm + (Tc - Tm) * (yg - s) / (n - s);
+    return Tm + (Tcol[k] - Tm) * (yg - s) / ((k + 0.5) - s);
 }
 
 /* ------------------------------------------------------------- geometry */
@@ -437,7 +526,9 @@ static void cell_u(const orc_sim *S, long c, real T, real *u) {
 /* Ghost temperature and ghost-node post-collision populations of every
    column, from the current state: g*_ghost = g^eq(T_ghost, 0) +
    (g*_L - g^eq(T_L, u_L)), L the liquid node below the ghost (none: the
-   equilibrium alone). */
+   equilibrium alone).  With solid conduction also the solid side's ghost at
+   the last liquid node: g^eq(T_sghost, 0) + (g*_S - g^eq(T_S, 0)), S the
+   solid node above it (collided at u = 0 with the solid's rates). */
 static void refresh_ghosts(orc_sim *S) {
     real *Tcol = (real *)malloc(sizeof(real) * S->H);
     real zero[3] = {0.0, 0.0, 0.0};
@@ -455,6 +546,17 @@ static void refresh_ghosts(orc_sim *S) {
             collide_g(S->Nm, S->Ninv, S->Qr, S->g + L * Q7, uL, gsL);
             geq7(Tcol[js - 1], uL, geL);
             for (int i = 0; i < Q7; ++i) gp[i] += gsL[i] - geL[i];
+        }
+        if (S->cfg.solid) {
+            real *sp = S->Spost + col * Q7;
+            geq7(solid_ghost_T(Tcol, S->H, S->s[col], S->cfg.Tc, S->cfg.Tm), zero, sp);
+            if (js >= 1 && js < S->H) {
+                long Sn = column_cell(S, col, js);
+                real gsS[Q7], geS[Q7];
+                collide_g(S->Nm, S->Ninv, S->Qs, S->g + Sn * Q7, zero, gsS);
+                geq7(Tcol[js], zero, geS);
+                for (int i = 0; i < Q7; ++i) sp[i] += gsS[i] - geS[i];
+            }
         }
     }
     free(Tcol);
@@ -510,6 +612,14 @@ static int derive(orc_sim *S) {
     memcpy(S->S, sr, sizeof sr);
     real qr[Q7] = {1.0, S->s_alpha_r, S->s_alpha_r, S->s_alpha_r, c->s_g4, c->s_g5, c->s_g5};
     memcpy(S->Qr, qr, sizeof qr);
+    /* Solid conduction: alpha_s = (k_s / k_l) alpha (equal rho c), the same
+       D3Q7 basis and higher-order rates. */
+    if (c->solid != 0 && c->solid != 1) return set_err(S, "solid must be 0 or 1");
+    if (c->solid && !(c->ks_kl > 0.0)) return set_err(S, "ks_kl must be > 0");
+    S->alpha_s = c->solid ? c->ks_kl * S->alpha : S->alpha;
+    real sas = 1.0 / (S->alpha_s / CS2T + 0.5);
+    real qs[Q7] = {1.0, sas, sas, sas, c->s_g4, c->s_g5, c->s_g5};
+    memcpy(S->Qs, qs, sizeof qs);
     return ORC_OK;
 }
 
@@ -538,20 +648,27 @@ orc_sim *orc_create(const orc_cfg *cfg, char *err, int errlen) {
     S->Thw = (real *)calloc(S->ncols, sizeof(real));
     S->js = (int *)calloc(S->ncols, sizeof(int));
     S->Gpost = (real *)calloc((size_t)S->ncols * Q7, sizeof(real));
+    S->Spost = (real *)calloc((size_t)S->ncols * Q7, sizeof(real));
     S->liq = (unsigned char *)calloc(S->N, 1);
     if (!S->f || !S->fs || !S->g || !S->gs || !S->s || !S->snew || !S->Tghost || !S->Thw || !S->js ||
-        !S->Gpost || !S->liq) {
+        !S->Gpost || !S->Spost || !S->liq) {
         if (err) snprintf(err, errlen, "out of memory");
         free(S->f); free(S->fs); free(S->g); free(S->gs); free(S->s); free(S->snew);
-        free(S->Tghost); free(S->Thw); free(S->js); free(S->Gpost); free(S->liq); free(S);
+        free(S->Tghost); free(S->Thw); free(S->js); free(S->Gpost); free(S->Spost); free(S->liq); free(S);
         return NULL;
     }
     const orc_cfg *c = &S->cfg;
     /* Initial state: front at s0; liquid at the Neumann temperature of that
        front, T = Th - (Th - Tm) erf(a / (2 sqrt(alpha t0))) / erf(lambda) with
        t0 = s0^2 / (4 lambda^2 alpha); at rest, rho = 1.  With Ste = 0 (front
-       held fixed) the liquid starts at Tm.  Solid at Tm. */
-    S->lambda = orc_neumann_lambda(c->Ste);
+       held fixed) the liquid starts at Tm.  Solid at Tm; with solid
+       conduction and Tc < Tm, lambda is the two-phase one and the solid is at
+       T = Tc + (Tm - Tc) erfc(a / (2 sqrt(alpha_s t0))) / erfc(lambda /
+       sqrt(kappa)) (at Tc when Ste = 0). */
+    const int subcooled = c->solid && c->Tc < c->Tm;
+    const double kappa = c->solid ? c->ks_kl : 1.0;
+    S->lambda = subcooled ? orc_neumann_lambda2(c->Ste, (c->Tm - c->Tc) / (c->Th - c->Tm), kappa)
+                          : orc_neumann_lambda(c->Ste);
     S->t0 = c->Ste > 0.0 ? c->s0 * c->s0 / (4.0 * S->lambda * S->lambda * RE(S->alpha)) : 0.0;
     for (long col = 0; col < S->ncols; ++col) {
         S->s[col] = c->s0;
@@ -569,6 +686,13 @@ orc_sim *orc_create(const orc_cfg *cfg, char *err, int errlen) {
             if (c->Ste > 0.0)
                 T = c->Th - (c->Th - c->Tm) * erf(a / (2.0 * sqrt(RE(S->alpha) * S->t0))) / erf(S->lambda);
             feq19(1.0, zero, S->f + cc * Q19);
+        } else if (subcooled) {
+            /* alpha_s t0 = kappa s0^2 / (4 lambda^2) */
+            T = c->Tc;
+            if (c->Ste > 0.0) {
+                double r = sqrt(kappa);
+                T = c->Tc + (c->Tm - c->Tc) * erfc(S->lambda * a / (r * c->s0)) / erfc(S->lambda / r);
+            }
         }
         geq7(T, zero, S->g + cc * Q7);
     }
@@ -579,7 +703,7 @@ orc_sim *orc_create(const orc_cfg *cfg, char *err, int errlen) {
 void orc_destroy(orc_sim *S) {
     if (!S) return;
     free(S->f); free(S->fs); free(S->g); free(S->gs); free(S->s); free(S->snew);
-    free(S->Tghost); free(S->Thw); free(S->js); free(S->Gpost); free(S->liq);
+    free(S->Tghost); free(S->Thw); free(S->js); free(S->Gpost); free(S->Spost); free(S->liq);
     free(S);
 }
 
@@ -600,6 +724,11 @@ static void collide_all(orc_sim *S) {
             real u[3];
             collide_f(S->M, S->Minv, S->S, S->f + c * Q19, F, S->fs + c * Q19, u);
             collide_g(S->Nm, S->Ninv, S->Qr, g, u, S->gs + c * Q7);
+        } else if (S->cfg.solid) {
+            /* heat conduction in the solid: D3Q7 MRT at u = 0 */
+            real zero[3] = {0.0, 0.0, 0.0};
+            collide_g(S->Nm, S->Ninv, S->Qs, S->g + c * Q7, zero, S->gs + c * Q7);
+            for (int i = 0; i < Q19; ++i) S->fs[c * Q19 + i] = 0.0;
         } else {
             long col = column_of(S, x, y, z);
             int j = axial_of(S, x, y, z);
@@ -626,6 +755,23 @@ static int wall_kind7(const orc_sim *S, int x, int y, int z, int i) {
     return up < 0 ? 1 : 2;
 }
 
+/* With solid conduction: the D3Q7 population that streams from node u to
+   its neighbour c along direction i.  Within a phase it is u's own
+   post-collision value; across the phase boundary it is u's ghost
+   population for c's phase when u is its column's ghost for that phase (the
+   first solid node for a liquid c, the last liquid node for a solid c), else
+   the rest state at Tm. */
+static real crossing_g(const orc_sim *S, long u, long c, int i) {
+    if (S->liq[u] == S->liq[c]) return S->gs[u * Q7 + i];
+    int x, y, z;
+    coords(S, u, &x, &y, &z);
+    long col = column_of(S, x, y, z);
+    int j = axial_of(S, x, y, z);
+    if (S->liq[u]) /* a solid c */
+        return j == S->js[col] - 1 ? S->Spost[col * Q7 + i] : w7(i) * S->cfg.Tm;
+    return j == S->js[col] ? S->Gpost[col * Q7 + i] : w7(i) * S->cfg.Tm;
+}
+
 static void stream_all(orc_sim *S) {
     #pragma omp parallel for schedule(static)
     for (long c = 0; c < S->N; ++c) {
@@ -648,7 +794,8 @@ static void stream_all(orc_sim *S) {
         for (int i = 0; i < Q7; ++i) {
             int kind = wall_kind7(S, x, y, z, i);
             if (kind == 0) {
-                gn[i] = S->gs[cell_index(S, x - TX[i], y - TY[i], z - TZ[i]) * Q7 + i];
+                long u = cell_index(S, x - TX[i], y - TY[i], z - TZ[i]);
+                gn[i] = S->cfg.solid ? crossing_g(S, u, c, i) : S->gs[u * Q7 + i];
             } else if (kind == 3) { /* adiabatic wall: bounce-back */
                 gn[i] = S->gs[c * Q7 + opp7(i)];
             } else { /* isothermal wall: anti-bounce-back -g*_opp + 2 w_i Tw */
@@ -678,6 +825,8 @@ static void stream_all(orc_sim *S) {
 /* Eq. 6 with k_s = k_l, a solid held at Tm (zero subcooling, so the solid-side
    gradient vanishes) and rho_l h_sl / k_l = Ste / (alpha (Th - Tm)) in lattice
    units:  ds/dt = alpha Ste / (Th - Tm) (1 + s_p^2 + s_q^2) (-dT_l/da).
+   With solid conduction the solid side's term enters:
+   ds/dt = alpha Ste / (Th - Tm) (1 + s_p^2 + s_q^2) (kappa dT_s/da - dT_l/da).
    In-plane slopes by central differences, mirror ghost at the side walls.
    All columns read the old s (Jacobi). */
 static int front_update(orc_sim *S) {
@@ -695,7 +844,11 @@ static int front_update(orc_sim *S) {
         real sp = 0.5 * (sp_hi - sp_lo), sq = 0.5 * (sq_hi - sq_lo);
         column_T(S, col, Tcol);
         real G = front_gradient(Tcol, S->H, S->s[col], S->Thw[col], c->Tm);
-        real v = coef * (1.0 + sp * sp + sq * sq) * (-G);
+        /* solid conduction: + (k_s / k_l) dT_s/da, in a column with a solid node */
+        real Gs = 0.0;
+        if (c->solid && n_liquid(S->s[col], S->H) < S->H)
+            Gs = c->ks_kl * solid_gradient(Tcol, S->H, S->s[col], c->Tc, c->Tm);
+        real v = c->solid ? coef * (1.0 + sp * sp + sq * sq) * (Gs - G) : coef * (1.0 + sp * sp + sq * sq) * (-G);
         if (!(fabs(RE(v)) <= 0.5)) bad = 1;
         real sn = S->s[col] + v;
         if (RE(sn) < 0.5) sn = 0.5;
@@ -745,10 +898,11 @@ int orc_step(orc_sim *S, long nsteps) {
 /* --------------------------------------------------------------- outputs */
 
 /* T and u per node (liquid: T = sum g, u = (sum f e + F/2)/rho0; solid:
-   T = Tm, u = 0), the front heights, and the liquid fraction sum(s)/(H ncols). */
+   T = Tm, or sum g with solid conduction, u = 0), the front heights, and the
+   liquid fraction sum(s)/(H ncols). */
 void orc_get(const orc_sim *S, double *T, double *u, double *s, double *lf) {
     for (long c = 0; c < S->N; ++c) {
-        real Tc = S->cfg.Tm, uc[3] = {0.0, 0.0, 0.0};
+        real Tc = S->cfg.solid ? cell_T(S, c) : S->cfg.Tm, uc[3] = {0.0, 0.0, 0.0};
         if (S->liq[c]) {
             Tc = cell_T(S, c);
             const real *f = S->f + c * Q19;
@@ -809,7 +963,8 @@ void orc_get_state(const orc_sim *S, double *f, double *g, double *s) {
 /* Replace the state; flags and ghost nodes are recomputed from s and g.  A
    solid node's own populations never enter the method (its post-collision
    values are reset every step), so solid nodes are stored at rest: f = 0,
-   g = g^eq(Tm, 0). */
+   g = g^eq(Tm, 0).  With solid conduction a solid node keeps the given g
+   (f = 0). */
 void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s) {
     if (s)
         for (long col = 0; col < S->ncols; ++col) S->s[col] = s[col];
@@ -821,7 +976,8 @@ void orc_set_state(orc_sim *S, const double *f, const double *g, const double *s
             for (int i = 0; i < Q19; ++i) S->f[c * Q19 + i] = S->liq[c] ? f[(long)i * S->N + c] : 0.0;
     if (g)
         for (long c = 0; c < S->N; ++c)
-            for (int i = 0; i < Q7; ++i) S->g[c * Q7 + i] = S->liq[c] ? g[(long)i * S->N + c] : gm[i];
+            for (int i = 0; i < Q7; ++i)
+                S->g[c * Q7 + i] = (S->liq[c] || S->cfg.solid) ? g[(long)i * S->N + c] : gm[i];
     refresh_ghosts(S);
 }
 
@@ -834,17 +990,22 @@ void orc_set_hot_wall(orc_sim *S, const double *Thw) {
 
 /* info[0..]: nu, alpha, gbeta, lambda, t0, s_nu, s_alpha, H, steps, q_hot,
    q_cold, liquid mass (sum rho over liquid nodes), liquid node count,
-   sum of T over liquid nodes. */
+   sum of T over liquid nodes, sum of T over solid nodes (Tm each without
+   solid conduction), alpha_s. */
 void orc_info(const orc_sim *S, double *info) {
-    double mass = 0.0, nl = 0.0, eT = 0.0;
+    double mass = 0.0, nl = 0.0, eT = 0.0, eS = 0.0;
     for (long c = 0; c < S->N; ++c) {
-        if (!S->liq[c]) continue;
+        if (!S->liq[c]) {
+            eS += S->cfg.solid ? RE(cell_T(S, c)) : S->cfg.Tm;
+            continue;
+        }
         for (int i = 0; i < Q19; ++i) mass += RE(S->f[c * Q19 + i]);
         eT += RE(cell_T(S, c));
         nl += 1.0;
     }
-    double v[14] = {RE(S->nu), RE(S->alpha), RE(S->gbeta), S->lambda, S->t0, RE(S->s_nu_r), RE(S->s_alpha_r),
-                    (double)S->H, (double)S->steps, RE(S->q_hot), RE(S->q_cold), mass, nl, eT};
+    double v[16] = {RE(S->nu), RE(S->alpha), RE(S->gbeta), S->lambda, S->t0, RE(S->s_nu_r), RE(S->s_alpha_r),
+                    (double)S->H, (double)S->steps, RE(S->q_hot), RE(S->q_cold), mass, nl, eT, eS,
+                    RE(S->alpha_s)};
     memcpy(info, v, sizeof v);
 }
 
@@ -921,6 +1082,15 @@ double orc_front_gradient(const double *Tcol, int n, double s, double Tw, double
 
 double orc_ghost_T(const double *Tcol, int n, double s, double Tw, double Tm) {
     return ghost_T(Tcol, n, s, Tw, Tm);
+}
+
+/* Solid-side front gradient and ghost temperature of one column. */
+double orc_solid_gradient(const double *Tcol, int n, double s, double Tc, double Tm) {
+    return solid_gradient(Tcol, n, s, Tc, Tm);
+}
+
+double orc_solid_ghost_T(const double *Tcol, int n, double s, double Tc, double Tm) {
+    return solid_ghost_T(Tcol, n, s, Tc, Tm);
 }
 #else
 /* --------------------------------------------- complex-step (tangent) API */
