@@ -248,6 +248,38 @@ lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, in
    (lbm_melt_set_timing) run step by step.  steps in [0, 256]. */
 lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps);
 
+/* Heat conduction in the solid: the k_s dT_s/da term of Eq. 6, for a cold
+   wall below the melting point (Tc < Tm, a subcooled solid; the paper
+   solves only zero subcooling, where the solid stays at Tm and the term
+   vanishes -- the default).  ks_kl = k_s / k_l > 0 turns it on, 0 turns it
+   off.  With it on:
+   - the solid (equal rho c in both phases, so alpha_s = ks_kl alpha) runs
+     the D3Q7 collision of Eq. 4 at u = 0 with that diffusivity, and its
+     populations stream among solid nodes and against the walls like the
+     liquid's (Tc at the cold wall);
+   - the front is a T = Tm surface on both sides: the solid side's ghost is
+     the last liquid node of a column, at the temperature extrapolated
+     through (s, Tm) and the lowest solid node at least half a cell above s
+     (the cold wall standing in), plus the non-equilibrium part of the solid
+     node above it; a population crossing the phase boundary from a node
+     that is not its column's ghost for the receiving phase is the rest
+     state at Tm;
+   - Eq. 6 reads ds/dt = alpha Ste / (Th - Tm) (1 + s_x^2 + s_z^2)
+     (ks_kl dT_s/da - dT_l/da), with dT_s/da the one-sided quadratic through
+     (s, Tm) and the two lowest solid nodes at least half a cell above s (the
+     cold wall standing in for a missing one);
+   - lbm_melt_get reports the solid's own temperature; lbm_melt_set_state
+     keeps the g given for solid nodes; every node is updated every step
+     (no deep-solid skip).
+   Only before the first step: the call re-initialises the state, the
+   liquid below s0 and the solid above it at the two-phase Neumann solution
+   of conduction melting against a solid initially at Tc (lambda and t0 of
+   lbm_melt_get_info follow it), and resets the heated-wall field to the
+   scalar Th.  Rejected (LBM_EINVAL) for an ensemble member; the adjoint
+   (lbm_melt_tape_forward) rejects a handle with conduction on.
+   Synchronises. */
+lbm_status lbm_melt_set_solid_conduction(lbm_melt *h, double ks_kl);
+
 const char *lbm_melt_last_error(const lbm_melt *h);
 void lbm_melt_destroy(lbm_melt *h);
 

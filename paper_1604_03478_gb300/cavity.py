@@ -49,11 +49,14 @@ class Cavity:
     (0: y = 0, 1: z = 0), storage precision (0 fp32, 1 fp16), Ma, initial
     front s0, Ra, Pr, Ste, Th, Tc, Tm and the rates (``derive`` takes s_nu,
     s_alpha from Ra, Pr, Ma and H).  ``stream`` is a cudaStream_t as int
-    (default: torch's current stream).
+    (default: torch's current stream).  ``solid=1`` turns on heat conduction
+    in the solid with conductivity ratio ``ks_kl`` = k_s / k_l
+    (lbm_melt_set_solid_conduction).
     """
 
     def __init__(self, nx, ny, nz, face=0, precision=0, Ra=0.0, Pr=1.0, Ste=0.1, Th=1.0, Tc=0.0, Tm=0.0,
-                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, stream=None, **rates):
+                 Ma=0.1, s0=1.0, s_nu=1.0, s_alpha=1.0, derive=False, stream=None, solid=0, ks_kl=1.0,
+                 **rates):
         L = _abi.load()
         self.grid, self.rates = make_args(nx, ny, nz, face, precision, Ma, s0, s_nu, s_alpha, derive, **rates)
         if stream is None:
@@ -73,6 +76,8 @@ class Cavity:
         self.H = ny if face == 0 else nz
         self.cols_shape = (nz, nx) if face == 0 else (ny, nx)
         self.ncols = self.cols_shape[0] * self.cols_shape[1]
+        if solid:
+            self.set_solid_conduction(ks_kl)
 
     @classmethod
     def _member(cls, handle, nx, ny, nz, face):
@@ -202,6 +207,11 @@ class Cavity:
 
     def set_timing(self, on=True):
         self._check(_abi.load().lbm_melt_set_timing(self._h, 1 if on else 0))
+
+    def set_solid_conduction(self, ks_kl):
+        """Heat conduction in the solid with k_s / k_l = ks_kl (0: off);
+        before the first step, re-initialises the state."""
+        self._check(_abi.load().lbm_melt_set_solid_conduction(self._h, float(ks_kl)))
 
     def set_graph_steps(self, steps):
         """Steps per CUDA-graph replay in step() (0: step by step)."""

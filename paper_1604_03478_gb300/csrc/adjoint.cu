@@ -713,6 +713,9 @@ void lbm_tape_free(lbm_melt *h) { free_tape(h); }
 LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every) {
     if (!h) return LBM_EINVAL;
     if (steps < 1) return tape_err(h, LBM_EINVAL, "steps must be >= 1");
+    if (h->kp.cond)
+        return tape_err(h, LBM_EINVAL, "the adjoint differentiates the method with the solid held at Tm "
+                                       "(no heat conduction in the solid)");
     if (h->thw_pending)
         return tape_err(h, LBM_EINVAL, "set the heated-wall field before recording (no change may be pending)");
     if (ckpt_every <= 0) ckpt_every = (long long)std::ceil(std::sqrt((double)steps));

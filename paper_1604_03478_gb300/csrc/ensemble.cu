@@ -235,6 +235,7 @@ LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *
         lbm_melt *h = nullptr;
         lbm_status st = lbm_melt_create(&c.grid, c.Ra, c.Pr, c.Ste, c.Th, c.Tc, c.Tm, &c.rates, (void *)e->stream, &h);
         if (st != LBM_OK) return fail(st);
+        h->member = 1;
         e->cav.push_back(h);
         // the persistent kernel's even step indexes a member's state in 32 bits
         if (19LL * h->kp.ld >= (1LL << 32)) return fail(LBM_EINVAL);

@@ -69,6 +69,12 @@ struct lbm_melt {
     long long exec_steps;        // steps this handle executed (never rewound)
     double Ra;         // as given to create
     int derived_from_Ra;
+    // Heat conduction in the solid (lbm_melt_set_solid_conduction): the
+    // conductivity ratio k_s / k_l (0: off, the solid held at Tm) and the
+    // solid side's ghost populations of each column (7 x ncols).
+    double ks_kl;
+    float *spost;
+    int member;        // owned by an ensemble (whose kernel holds the solid at Tm)
     void *tape;        // recorded run for the adjoint (adjoint.cu)
     // Steps replayed from CUDA graphs (lbm_melt_step): graph_steps steps per
     // replay (0: every step launched on its own).  One instantiated graph per

@@ -78,10 +78,43 @@ __device__ __forceinline__ bool deep_solid(const KP &p, int a, int nbv) {
     return p.skip_deep && a >= (nbv & 0xffff) + 2;
 }
 
+// ------------------------------------------------- conduction in the solid
+// Bit i (1..6): the D3Q7 link leaving node x along t_i ends inside the
+// cavity on a node of the other phase (liq: x is liquid).
+template <int FACE>
+__device__ __forceinline__ unsigned other_phase7(const KP &p, const int *__restrict__ js, int x, int y, int z,
+                                                 bool liq) {
+    unsigned m = 0;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) {
+        const int xn = x + tx(i), yn = y + ty(i), zn = z + tz(i);
+        if (inside(p, xn, yn, zn) && (axial<FACE>(xn, yn, zn) < __ldg(js + column<FACE>(p, xn, yn, zn))) != liq)
+            m |= 1u << i;
+    }
+    return m;
+}
+
+// With heat conduction in the solid, a population leaving node x towards a
+// node of the other phase (bits of `other`) is not x's own post-collision
+// value: it is the ghost population of x's column for the receiving phase
+// when x is that ghost (ghost: the first solid node towards the liquid, with
+// the liquid side's ghost populations gbuf; the last liquid node towards the
+// solid, with the solid side's), else the rest state at Tm.
+__device__ __forceinline__ void cross_phase(const KP &p, unsigned other, bool ghost, const float *__restrict__ gbuf,
+                                            int col, float (&g)[7]) {
+#pragma unroll
+    for (int i = 1; i < 7; ++i)
+        if ((other >> i) & 1u) g[i] = ghost ? __ldg(gbuf + (long long)i * p.ncols + col) : w7(i) * p.dTms;
+}
+
 // ------------------------------------------------------------- even step
-template <typename ST, int FACE, typename IX = long long>
+// COND: heat conduction in the solid (the solid collides its own g at u = 0
+// and the links across the phase boundary carry the ghost or rest values of
+// cross_phase; spost holds the solid side's ghost populations).
+template <typename ST, int FACE, typename IX = long long, bool COND = false>
 __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
-                                          const int *__restrict__ nb, const float *__restrict__ gpost, int x, int y, int z) {
+                                          const int *__restrict__ nb, const float *__restrict__ gpost, int x, int y,
+                                          int z, const float *__restrict__ spost = nullptr) {
     const IX c = (IX)node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
@@ -96,6 +129,18 @@ __device__ __forceinline__ void even_node(const KP &p, ST *__restrict__ F, ST *_
         collide(p, f, g);
 #pragma unroll
         for (int i = 0; i < 19; ++i) Store<ST>::st_stream(elem<IX>(F, c, opp(i) * p.ld), f[i]);
+        if (COND && a + 1 >= (__ldg(nb + col) >> 16)) {
+            const unsigned other = other_phase7<FACE>(p, js, x, y, z, true);
+            if (other) cross_phase(p, other, a == jsc - 1, spost, col, g);
+        }
+    } else if (COND) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) g[i] = Store<ST>::ld(elem<IX>(G, c, i * p.ld));
+        collide_solid(p, g);
+        if (a <= (__ldg(nb + col) & 0xffff)) {
+            const unsigned other = other_phase7<FACE>(p, js, x, y, z, false);
+            if (other) cross_phase(p, other, a == jsc, gpost, col, g);
+        }
     } else {
         if (deep_solid(p, a, __ldg(nb + col))) return;
         solid_post(p, a == jsc, gpost, col, g);
@@ -138,6 +183,15 @@ __global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_even(const __grid_
                                               const float *__restrict__ gpost, const int *jmax) {
     int x, y, z;
     if (k1_node<FACE>(p, jmax, x, y, z)) even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
+}
+
+// The even step with heat conduction in the solid (every node updated).
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_even_cond(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
+                                                   const int *__restrict__ js, const int *__restrict__ nb,
+                                                   const float *__restrict__ gpost, const float *__restrict__ spost) {
+    int x, y, z;
+    if (k1_node<FACE>(p, nullptr, x, y, z)) even_node<ST, FACE, long long, true>(p, F, G, js, nb, gpost, x, y, z, spost);
 }
 
 
@@ -188,11 +242,13 @@ __device__ __forceinline__ bool xwall(int ex_up, bool xlo, bool xhi) {
 // across an x wall, which bounce back (no-slip for f, adiabatic for g).  The
 // x walls are taken by selects inside the fast path, so that the warps that
 // hold x = 0 or x = nx - 1 do not split between two paths.
-template <typename ST, int FACE, bool TAB = true>
+//
+// COND: heat conduction in the solid (see even_node).
+template <typename ST, int FACE, bool TAB = true, bool COND = false>
 __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
                                          const int *__restrict__ nb, const float *__restrict__ gpost,
                                          const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
-                                         int y, int z) {
+                                         int y, int z, const float *__restrict__ spost = nullptr) {
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);
@@ -261,6 +317,30 @@ __device__ __forceinline__ void odd_node(const KP &p, const Links *lk, ST *__res
 #pragma unroll
         for (int i = 1; i < 19; ++i)
             Store<ST>::st_stream(((lm >> opp(i)) & 1u) ? Fc + fout_off<FACE, TAB>(p, lk, i) : Fc + opp(i) * p.ld, f[i]);
+        if (COND) {
+            // x + t_i = x - e_opp(i): inside (bit opp(i) of im) and solid (bit opp(i) of lm clear)
+            unsigned other = 0;
+#pragma unroll
+            for (int i = 1; i < 7; ++i)
+                if (((im >> opp7(i)) & 1u) && !((lm >> opp(i)) & 1u)) other |= 1u << i;
+            if (other) cross_phase(p, other, a == jsc - 1, spost, col, g);
+        }
+    } else if (COND) {
+        // the solid's own g: pulled as for a liquid node, collided at u = 0
+        const unsigned ims = off_walls ? 0x7eu : inside_mask(p, x, y, z);
+        const float th_rd = __ldg(thw_rd + col);
+        g[0] = Store<ST>::ld(Gc);
+#pragma unroll
+        for (int i = 1; i < 7; ++i) {
+            const bool in = (ims >> i) & 1u;
+            const float v = Store<ST>::ld(in ? Gc + gin_off<FACE, TAB>(p, lk, i) : Gc + i * p.ld);
+            g[i] = in ? v : wall_value<FACE>(p, opp7(i), v, th_rd);
+        }
+        collide_solid(p, g);
+        if (a <= (nbv & 0xffff)) {
+            const unsigned other = other_phase7<FACE>(p, js, x, y, z, false);
+            if (other) cross_phase(p, other, a == jsc, gpost, col, g);
+        }
     } else {
         if (deep_solid(p, a, nbv)) return;
         solid_post(p, a == jsc, gpost, col, g);
@@ -284,6 +364,18 @@ __global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_odd(const __grid_c
                                              const int *jmax) {
     int x, y, z;
     if (k1_node<FACE>(p, jmax, x, y, z)) odd_node<ST, FACE>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+}
+
+// The odd step with heat conduction in the solid (every node updated).
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_odd_cond(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
+                                                  const int *__restrict__ js, const int *__restrict__ nb,
+                                                  const float *__restrict__ gpost, const float *__restrict__ thw_rd,
+                                                  const float *__restrict__ thw_wr, const __grid_constant__ Links lk,
+                                                  const float *__restrict__ spost) {
+    int x, y, z;
+    if (k1_node<FACE>(p, nullptr, x, y, z))
+        odd_node<ST, FACE, true, true>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z, spost);
 }
 
 
@@ -406,6 +498,26 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
     return k > H - 1 ? H - 1 : (k < 0 ? -1 : k);
 }
 
+// Lowest node at least half a cell above s (centre j + 1/2 >= s + 1/2, i.e.
+// j = ceil(s)), or H when there is none.
+__device__ __forceinline__ int guarded_solid_node(double s, int H) {
+    const int k = (int)ceil(s);
+    return k > H ? H : k;
+}
+
+// Solid-side dT/da at the front a = s (the k_s dT_s/da term of Eq. 6, heat
+// conduction in the solid): the mirror of front_gradient, the one-sided
+// quadratic through (s, Tm), the guarded solid node ks and the node above
+// it, the cold wall (H, Tc) standing in for a missing node; linear through
+// (s, Tm) and (H, Tc) when ks = H.  Y1, Y2: the temperatures of nodes ks and
+// ks + 1 (or the wall) minus Tm, so that a solid at Tm gives exactly zero.
+__device__ __forceinline__ float solid_gradient(int ks, int H, double sc, float Y1, float Y2, float Tm, float Tc) {
+    if (ks >= H) return (Tc - Tm) / (float)((double)H - sc);
+    const double x1 = ks + 0.5, x2 = ks + 1 < H ? ks + 1.5 : (double)H;
+    return Y1 * (float)(sc - x2) / ((float)(x1 - sc) * (float)(x1 - x2)) +
+           Y2 * (float)(sc - x1) / ((float)(x2 - sc) * (float)(x2 - x1));
+}
+
 // ------------------------------------------------------------ front (Eq. 6)
 // One thread per column.  From the state after a step (T of the liquid at
 // t + 1, front s_t): the one-sided quadratic gradient at the front, the
@@ -423,12 +535,20 @@ __device__ __forceinline__ int guarded_node(double s, int H) {
 // precision of the temperatures they are made of.  GB300 issues FP64 at a
 // small fraction of its FP32 rate, and the FP64 divisions of an all-FP64
 // version made this kernel FP64-pipe bound.
-template <typename ST, int FACE, bool SPEC = true>
+//
+// COND (heat conduction in the solid): Eq. 6 gains kappa dT_s/da from
+// solid_gradient at s_t, and the solid side's ghost populations of the new
+// front are written to spost: at the last liquid node, g^eq(T_sghost, 0)
+// plus the non-equilibrium part of the first solid node collided at u = 0,
+// with T_sghost on the line through (s, Tm) and the guarded solid node (or
+// the cold wall); the rest state at Tm in a column without both phases.
+template <typename ST, int FACE, bool SPEC = true, bool COND = false>
 __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ F, const ST *__restrict__ G,
                                            const int *__restrict__ js, int *__restrict__ js_next,
                                            const double *__restrict__ s, double *__restrict__ s_next,
                                            float *__restrict__ gpost, const float *__restrict__ thw, int inflight,
-                                           int move, int *__restrict__ status, int col) {
+                                           int move, int *__restrict__ status, int col,
+                                           float *__restrict__ spost = nullptr) {
     const int P1 = p.P1, P2 = p.P2, H = p.H;
     const int pp = col % P1, q = col / P1;
     const bool infl = inflight != 0;
@@ -463,12 +583,24 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
         if (infl) gather_f9<ST, FACE>(p, F, js9, x, y, z, L, fL);
         else gather_f<ST, FACE>(p, F, js, x, y, z, false, fL);
     }
+    // The solid side of the front (conduction in the solid, a column with a
+    // solid node): temperatures of the guarded solid node and the one above.
+    int ks = H;
+    float Ts1 = Tm, Ts2 = Tm, Gs = 0.0f;
+    if (COND && move && jsc < H) {
+        ks = guarded_solid_node(sc, H);
+        if (ks < H) {
+            Ts1 = node_T<ST, FACE>(p, G, col, ks, infl, thw);
+            Ts2 = ks + 1 < H ? node_T<ST, FACE>(p, G, col, ks + 1, infl, thw) : p.Tc;
+        }
+        Gs = p.kappa * solid_gradient(ks, H, sc, Ts1 - Tm, Ts2 - Tm, Tm, p.Tc);
+    }
     // Then Eq. 6.
     double sn = sc;
     if (move) {
         const float Gr = front_gradient(k, sc, y0, y1, Tm, Tw);
-        const float v = front_speed(p, front_slope_factor(sp, sq), Gr);
-        if (!isfinite(Gr)) atomicOr(status, 2);
+        const float v = front_speed(p, front_slope_factor(sp, sq), COND ? Gr - Gs : Gr);
+        if (!isfinite(Gr) || (COND && !isfinite(Gs))) atomicOr(status, 2);
         else if (!(fabsf(v) <= 0.5f)) atomicOr(status, 1);
         sn = sc + (double)v;
         if (!(sn >= 0.5)) sn = 0.5;  // also catches NaN
@@ -478,6 +610,50 @@ __device__ __forceinline__ int front_column(const KP &p, const ST *__restrict__ 
     int jn = (int)ceil(sn - 0.5);
     jn = jn < 0 ? 0 : (jn > H ? H : jn);
     js_next[col] = jn;
+    if (COND) {
+        // the solid side's ghost populations at the last liquid node jn - 1
+        float sg[7];
+        if (jn >= 1 && jn < H) {
+            const double yg = jn - 0.5;
+            const int ks2 = guarded_solid_node(sn, H);
+            float Tsg;
+            if (ks2 >= H) {
+                Tsg = Tm + (p.Tc - Tm) * (float)((yg - sn) / ((double)H - sn));
+            } else {
+                float Tk;
+                if (move && jsc < H && ks2 == ks) Tk = Ts1;
+                else if (move && jsc < H && ks2 == ks + 1 && ks + 1 < H) Tk = Ts2;
+                else Tk = node_T<ST, FACE>(p, G, col, ks2, infl, thw);
+                Tsg = Tm + (Tk - Tm) * (float)((yg - sn) / ((ks2 + 0.5) - sn));
+            }
+            float gS[7];
+            int x, y, z;
+            column_node<FACE>(p, col, jn, x, y, z);
+            gather_g<ST, FACE>(p, G, x, y, z, infl, thw, gS);
+            const float Th = gS[0] + gS[1] + gS[2] + gS[3] + gS[4] + gS[5] + gS[6];
+            const float dTg = Tsg - p.Ts;
+#pragma unroll
+            for (int i = 0; i < 7; ++i) sg[i] = w7(i) * dTg;
+            // N^-1 (I - Q)(n - n^eq) of the solid node at u = 0
+            constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+            constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+            const float ra = 1.0f - p.s_alpha_s, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
+            float cn[7];
+            cn[0] = 0.0f;
+            cn[1] = ra * (gS[1] - gS[2]) * i1;
+            cn[2] = ra * (gS[3] - gS[4]) * i1;
+            cn[3] = ra * (gS[5] - gS[6]) * i1;
+            cn[4] = r4 * (6.0f * gS[0] - (gS[1] + gS[2] + gS[3] + gS[4] + gS[5] + gS[6]) - 0.75f * Th) * i4;
+            cn[5] = r5 * (2.0f * (gS[1] + gS[2]) - (gS[3] + gS[4] + gS[5] + gS[6])) * i5;
+            cn[6] = r5 * ((gS[3] + gS[4]) - (gS[5] + gS[6])) * i6;
+            add_back7<0>(sg, cn);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) sg[i] = w7(i) * p.dTms;
+        }
+#pragma unroll
+        for (int i = 0; i < 7; ++i) spost[(long long)i * p.ncols + col] = sg[i];
+    }
     if (jn >= H) return jn;  // fully liquid column: no ghost node
     const double yg = jn + 0.5;
     const int kg = guarded_node(sn, H);
@@ -558,6 +734,20 @@ __global__ void __launch_bounds__(128) k_front(const __grid_constant__ KP p, con
     // blocks are whole warps and every thread of the grid reaches this point
     const int m = __reduce_max_sync(0xffffffffu, jn);
     if (jmax && (threadIdx.x & 31) == 0 && m >= 0) atomicMax(jmax, m);
+}
+
+// The front update with heat conduction in the solid.
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(128) k_front_cond(const __grid_constant__ KP p, const ST *__restrict__ F,
+                                                    const ST *__restrict__ G, const int *__restrict__ js,
+                                                    int *__restrict__ js_next, const double *__restrict__ s,
+                                                    double *__restrict__ s_next, float *__restrict__ gpost,
+                                                    float *__restrict__ spost, const float *__restrict__ thw,
+                                                    int inflight, int move, int *__restrict__ status) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col < p.ncols)
+        front_column<ST, FACE, true, true>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col,
+                                           spost);
 }
 
 
@@ -641,7 +831,8 @@ __global__ void __launch_bounds__(128) k_flip(const __grid_constant__ KP p, ST *
 
 
 // ----------------------------------------------------- outputs and inputs
-// T and u per node (solid: Tm and 0), natural values.
+// T and u per node (solid: Tm, or its own temperature with heat conduction
+// in the solid, and u = 0), natural values.
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_macro(const __grid_constant__ KP p, const ST *__restrict__ F, const ST *__restrict__ G,
                                                const int *__restrict__ js, const float *__restrict__ thw,
@@ -664,6 +855,10 @@ __global__ void __launch_bounds__(128) k_macro(const __grid_constant__ KP p, con
         for (int i = 0; i < 19; ++i) { ux += ex(i) * f[i]; uy += ey(i) * f[i]; uz += ez(i) * f[i]; }
         uz += 0.5f * p.gbeta * (Th - p.dTms);
         Tc = p.Ts + Th;
+    } else if (p.cond) {
+        float g[7];
+        gather_g<ST, FACE>(p, G, x, y, z, inflight != 0, thw, g);
+        Tc = sum_T(p, g);
     }
     if (T) T[c] = Tc;
     if (u) { u[3 * c] = ux; u[3 * c + 1] = uy; u[3 * c + 2] = uz; }
@@ -706,7 +901,7 @@ __global__ void __launch_bounds__(128) k_state_out(const __grid_constant__ KP p,
 // Natural distributions in; leaves the natural layout.  A solid node's own
 // populations never enter the method (its post-collision values are reset
 // every step), so solid nodes are stored at rest: fh = 0 and gh = 0
-// (g at rest at Tm).
+// (g at rest at Tm); with heat conduction in the solid they keep their g.
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_state_in(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                                   const int *__restrict__ js, const float *__restrict__ fi,
@@ -721,14 +916,15 @@ __global__ void __launch_bounds__(128) k_state_in(const __grid_constant__ KP p, 
     if (gi)
 #pragma unroll
         for (int i = 0; i < 7; ++i)
-            Store<ST>::st(G + i * p.ld + c, liq ? gi[i * p.N + c] - w7(i) * p.Ts : w7(i) * p.dTms);
+            Store<ST>::st(G + i * p.ld + c, (liq || p.cond) ? gi[i * p.N + c] - w7(i) * p.Ts : w7(i) * p.dTms);
     if (fi)
 #pragma unroll
         for (int i = 0; i < 19; ++i) Store<ST>::st(F + i * p.ld + c, liq ? fi[i * p.N + c] - w19(i) : 0.0f);
 }
 
-// Initial state: fh = 0 everywhere (rest, rho = 1); gh = w (T(a) - Tm) with
-// the given profile below the front, 0 above.
+// Initial state: fh = 0 everywhere (rest, rho = 1); g at rest at the given
+// profile T(a) below the front and at Tm above (at the profile everywhere
+// with heat conduction in the solid).
 template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_init(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const float *__restrict__ Tprof) {
@@ -738,7 +934,7 @@ __global__ void __launch_bounds__(128) k_init(const __grid_constant__ KP p, ST *
     if (x >= p.nx || y >= p.ny) return;
     const long long c = node_index(p, x, y, z);
     const int a = axial<FACE>(x, y, z), col = column<FACE>(p, x, y, z);
-    const float dT = a < js[col] ? Tprof[a] - p.Ts : p.dTms;
+    const float dT = (a < js[col] || p.cond) ? Tprof[a] - p.Ts : p.dTms;
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store<ST>::st(F + i * p.ld + c, 0.0f);
 #pragma unroll

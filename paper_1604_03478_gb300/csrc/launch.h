@@ -26,6 +26,15 @@ struct Bufs {
     const float *thw_nu;         // heated-wall field of the last streaming (Nusselt number)
     double *nu;                  // per-column Nusselt numbers (ncols)
     double nu_scale;             // H / (alpha (Th - Tm))
+    float *spost;                // solid-side ghost populations, 7 x ncols (heat conduction in the solid)
+};
+
+// The stream-collide and front kernels with heat conduction in the solid
+// (KP::cond), in a translation unit of their own (k_cond.cu); Launch
+// forwards to them.
+template <typename ST> struct LaunchCond {
+    static cudaError_t stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st);
+    static cudaError_t front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st);
 };
 
 template <typename ST> struct Launch {

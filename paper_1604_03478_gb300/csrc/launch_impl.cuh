@@ -26,6 +26,7 @@ static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, d
 // 32-bit indices, 0.258 against 0.245 ms in FP32, and keeps 64-bit ones).
 template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
+    if (p.cond) return LaunchCond<ST>::stream_collide(p, face, odd, b, blk, st);
     const dim3 grd = k1_grid(p, blk, face, b.k1_height);
     if (19LL * p.ld < (1LL << 32)) launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
     else launch_sc<ST, long long>(p, face, odd, b, grd, blk, st);
@@ -34,6 +35,7 @@ cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Buf
 
 template <typename ST>
 cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, const Bufs &b, cudaStream_t st) {
+    if (p.cond) return LaunchCond<ST>::front(p, face, inflight, move, b, st);
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)

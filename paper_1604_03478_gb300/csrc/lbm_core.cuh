@@ -115,7 +115,13 @@ struct KP {
     double Tm_d, Th_d;
     double coef;      // alpha Ste / (Th - Tm): Eq. 6 front speed per unit -dT/da
     float coef_f;     // the same in FP32 (the front speed is FP32 arithmetic)
-    int skip_deep;    // Tc == Tm: deep solid nodes need no update
+    int skip_deep;    // Tc == Tm and no conduction in the solid: deep solid nodes need no update
+    // Heat conduction in the solid (Eq. 6's k_s term; off: the solid is held
+    // at Tm, the zero-subcooling case the paper solves): the solid runs the
+    // D3Q7 collision at u = 0 with the flux rate s_alpha_s of alpha_s =
+    // kappa alpha (equal rho c in both phases), kappa = k_s / k_l.
+    int cond;
+    float s_alpha_s, kappa;
 };
 
 // Element offsets of the interior odd step, relative to node c: f_i is
@@ -435,6 +441,28 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
     cn[6] = -p.s_g5 * n6 * i6;
     add_back7<0>(g, cn);
     if (uout) { uout[0] = ux; uout[1] = uy; uout[2] = uz; }
+}
+
+// Heat conduction in a solid node: the D3Q7 collision of Eq. 4 at u = 0 with
+// the solid's flux rate, n^eq = (T, 0, 0, 0, 3T/4, 0, 0); shifted
+// populations in and out.
+__device__ __forceinline__ void collide_solid(const KP &p, float (&g)[7]) {
+    const float Th = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    const float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
+    const float n4 = 6.0f * g[0] - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6]);
+    const float n5 = 2.0f * (g[1] + g[2]) - (g[3] + g[4] + g[5] + g[6]);
+    const float n6 = (g[3] + g[4]) - (g[5] + g[6]);
+    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+    float cn[7];
+    cn[0] = 0.0f;
+    cn[1] = -p.s_alpha_s * n1 * i1;
+    cn[2] = -p.s_alpha_s * n2 * i1;
+    cn[3] = -p.s_alpha_s * n3 * i1;
+    cn[4] = -p.s_g4 * (n4 - 0.75f * Th) * i4;
+    cn[5] = -p.s_g5 * n5 * i5;
+    cn[6] = -p.s_g5 * n6 * i6;
+    add_back7<0>(g, cn);
 }
 
 // ------------------------------------------------------------- geometry

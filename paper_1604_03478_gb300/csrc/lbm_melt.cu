@@ -50,6 +50,30 @@ double neumann_lambda(double Ste) {
     return 0.5 * (lo + hi);
 }
 
+// The two-phase Neumann solution of conduction melting against a solid
+// initially at Tc < Tm (conductivity ratio kappa = k_s / k_l, equal rho c,
+// so alpha_s = kappa alpha): the front is s = 2 lambda sqrt(alpha t), and the
+// one-dimensional interface balance (Eq. 6 without slopes) gives
+//   lambda sqrt(pi) / Ste = e^(-lambda^2) / erf(lambda)
+//                           - theta sqrt(kappa) e^(-lambda^2 / kappa) / erfc(lambda / sqrt(kappa)),
+// theta = (Tm - Tc) / (Th - Tm).  The left side grows and the right side
+// falls with lambda: bisection.  theta = 0 is neumann_lambda's equation.
+double neumann_lambda_two_phase(double Ste, double theta, double kappa) {
+    if (!(Ste > 0.0) || !(kappa > 0.0)) return 0.0;
+    const double rk = std::sqrt(kappa);
+    auto excess = [&](double l) {  // left side minus right side
+        return l * std::sqrt(M_PI) / Ste - std::exp(-l * l) / std::erf(l) +
+               theta * rk * std::exp(-l * l / kappa) / std::erfc(l / rk);
+    };
+    double lo = 0.0, hi = 1.0;
+    while (excess(hi) < 0.0) hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (excess(mid) < 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 double pick(double v, double dflt) { return v > 0.0 ? v : dflt; }
 
 lbm_status derive(const lbm_melt_grid *g, double Ra, double Pr, double Ste, double Th, double Tc, double Tm,
@@ -168,6 +192,7 @@ Bufs bufs_at(lbm_melt *h, int cur, int inflight) {
     b.thw_nu = inflight ? b.thw_rd : (h->thw_last_prev ? h->thw_prev : h->thw_cur);
     b.nu = h->nu_dev;
     b.nu_scale = (double)h->kp.H / (h->d.alpha * (h->Th - h->Tm));
+    b.spost = h->spost;
     return b;
 }
 
@@ -216,6 +241,7 @@ void free_all(lbm_melt *h) {
     cudaFree(h->nu_dev);
     cudaFree(h->report);
     cudaFree(h->jmax_dev);
+    cudaFree(h->spost);
     if (h->rb_val) cudaFreeHost(h->rb_val);
     for (int k = 0; k < lbm_melt::kRbRing; ++k)
         if (h->rb_ev[k]) cudaEventDestroy(h->rb_ev[k]);
@@ -401,6 +427,75 @@ cudaError_t lbm_enqueue_step(lbm_melt *h, int &cur, int &inflight, int height, c
 
 
 
+namespace {
+
+// The initial state (reading of the paper's initial condition: a front at s0
+// with the liquid below at the Neumann temperature of that front; with heat
+// conduction in a subcooled solid, the two-phase Neumann solution, the solid
+// above the front at its temperature), the liquid counts, 3x3 bounds and
+// ghost nodes of that state.  Synchronises.
+cudaError_t initial_state(lbm_melt *h) {
+    const Derived &d = h->d;
+    const KP &p = h->kp;
+    const double Th = h->Th, Tc = h->Tc, Tm = h->Tm, Ste = h->Ste;
+    const size_t nc = (size_t)d.ncols;
+    const size_t es = h->precision == 1 ? sizeof(__half) : sizeof(float);
+    const size_t nF = 19 * (size_t)p.ld * es, nG = 7 * (size_t)p.ld * es;
+    const bool subcooled = p.cond && Tc < Tm;
+    const double rk = std::sqrt(p.cond ? h->ks_kl : 1.0);
+    std::vector<float> Tprof(d.H);
+    for (int j = 0; j < d.H; ++j) {
+        const double a = j + 0.5;
+        double T = Tm;
+        if (a < d.s0) {
+            if (Ste > 0.0) T = Th - (Th - Tm) * std::erf(a / (2.0 * std::sqrt(d.alpha * d.t0))) / std::erf(d.lambda);
+        } else if (subcooled) {
+            // T = Tc + (Tm - Tc) erfc(a / (2 sqrt(alpha_s t0))) / erfc(lambda sqrt(alpha / alpha_s)),
+            // with alpha_s t0 = kappa s0^2 / (4 lambda^2)
+            T = Ste > 0.0 ? Tc + (Tm - Tc) * std::erfc(d.lambda * a / (rk * d.s0)) / std::erfc(d.lambda / rk) : Tc;
+        }
+        Tprof[j] = (float)T;
+    }
+    float *Tprof_dev = nullptr;
+    cudaError_t e = cudaMalloc(&Tprof_dev, sizeof(float) * d.H);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)((nc + 255) / 256);
+    e = cudaMemcpyAsync(Tprof_dev, Tprof.data(), sizeof(float) * d.H, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->F, 0, nF, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->G, 0, nG, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->js[0], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[0], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[1], 0, nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gpost, 0, 7 * nc * 4, h->stream);
+    if (e == cudaSuccess && h->spost) e = cudaMemsetAsync(h->spost, 0, 7 * nc * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) {
+        k_fill_d<<<nb, 256, 0, h->stream>>>(h->s[0], (long long)nc, d.s0);
+        k_fill_f<<<nb, 256, 0, h->stream>>>(h->thw_cur, (long long)nc, (float)Th);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        // liquid counts of the initial front (front held), then the initial
+        // distributions, then the ghost nodes of that state
+        h->cur = 0;
+        h->inflight = 0;
+        Bufs b = bufs(h);
+        e = LAUNCH(h, front, p, h->face, 0, 0, b, h->stream);
+        if (e == cudaSuccess) {
+            h->cur = 1;
+            b = bufs(h);
+            e = LAUNCH(h, init, p, h->face, b, Tprof_dev, h->stream);
+        }
+    }
+    if (e == cudaSuccess && refresh_front(h) != LBM_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(Tprof_dev);
+    return e;
+}
+
+}  // namespace
+
 LBM_API const char *lbm_melt_version(void) { return "lbm_melt 0.1 (sm_103a)"; }
 
 LBM_API lbm_status lbm_melt_derive(const lbm_melt_grid *grid, double Ra, double Pr, double Ste, double Th,
@@ -468,6 +563,9 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
     p.coef = Ste > 0.0 ? d.alpha * Ste / (Th - Tm) : 0.0;
     p.coef_f = (float)p.coef;
     p.skip_deep = (Tc == Tm) ? 1 : 0;
+    p.cond = 0;  // the solid held at Tm until lbm_melt_set_solid_conduction
+    p.kappa = 1.0f;
+    p.s_alpha_s = p.s_alpha;
     {
         const long long sy = p.nx, sz = (long long)p.nx * p.ny;
         for (int i = 0; i < 19; ++i) {
@@ -512,48 +610,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
         h->bytes += a.b;
     }
-    // Initial state (reading of the paper's initial condition: a front at s0
-    // with the liquid below at the Neumann temperature of that front).
-    std::vector<float> Tprof(d.H);
-    for (int j = 0; j < d.H; ++j) {
-        const double a = j + 0.5;
-        Tprof[j] = (float)(Ste > 0.0 ? Th - (Th - Tm) * std::erf(a / (2.0 * std::sqrt(d.alpha * d.t0))) /
-                                                std::erf(d.lambda)
-                                     : Tm);
-    }
-    float *Tprof_dev = nullptr;
-    if (cudaMalloc(&Tprof_dev, sizeof(float) * d.H) != cudaSuccess) return fail(LBM_ENOMEM);
-    const int nb = (int)((nc + 255) / 256);
-    cudaError_t e = cudaMemcpyAsync(Tprof_dev, Tprof.data(), sizeof(float) * d.H, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->F, 0, nF, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->G, 0, nG, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->js[0], 0, nc * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[0], 0, nc * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->nb[1], 0, nc * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->gpost, 0, 7 * nc * 4, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) {
-        k_fill_d<<<nb, 256, 0, h->stream>>>(h->s[0], (long long)nc, d.s0);
-        k_fill_f<<<nb, 256, 0, h->stream>>>(h->thw_cur, (long long)nc, (float)Th);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        // liquid counts of the initial front (front held), then the initial
-        // distributions, then the ghost nodes of that state
-        h->cur = 0;
-        h->inflight = 0;
-        Bufs b = bufs(h);
-        e = LAUNCH(h, front, p, h->face, 0, 0, b, h->stream);
-        if (e == cudaSuccess) {
-            h->cur = 1;
-            b = bufs(h);
-            e = LAUNCH(h, init, p, h->face, b, Tprof_dev, h->stream);
-        }
-    }
-    if (e == cudaSuccess && refresh_front(h) != LBM_OK) e = cudaErrorUnknown;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(Tprof_dev);
+    const cudaError_t e = initial_state(h);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
     if (seed_readback(h) != LBM_OK) return fail(LBM_ECUDA);
     *out = h;
@@ -886,6 +943,44 @@ LBM_API lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps) {
         h->graph_steps = steps;
     }
     return LBM_OK;
+}
+
+LBM_API lbm_status lbm_melt_set_solid_conduction(lbm_melt *h, double ks_kl) {
+    if (!h) return LBM_EINVAL;
+    if (h->member) return set_err(h, LBM_EINVAL, "an ensemble member keeps its solid at Tm");
+    if (h->steps != 0 || h->exec_steps != 0)
+        return set_err(h, LBM_EINVAL, "heat conduction in the solid is chosen before the first step");
+    if (!(ks_kl >= 0.0 && ks_kl <= 1e6))
+        return set_err(h, LBM_EINVAL, "k_s / k_l must be in (0, 1e6] (0 turns conduction in the solid off)");
+    const bool on = ks_kl > 0.0;
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    if (on && !h->spost) {
+        const size_t b = 7 * (size_t)h->kp.ncols * 4;
+        CK(cudaMalloc(&h->spost, b), "alloc solid ghosts");
+        h->bytes += b;
+    }
+    KP &p = h->kp;
+    const double alpha_s = on ? ks_kl * h->d.alpha : h->d.alpha;
+    p.cond = on ? 1 : 0;
+    p.kappa = (float)(on ? ks_kl : 1.0);
+    p.s_alpha_s = (float)(1.0 / (alpha_s / CS2T + 0.5));
+    p.skip_deep = (!on && h->Tc == h->Tm) ? 1 : 0;
+    h->ks_kl = on ? ks_kl : 0.0;
+    // the initial front's Neumann constant: two-phase against a subcooled solid
+    Derived &d = h->d;
+    d.lambda = (on && h->Tc < h->Tm)
+                   ? neumann_lambda_two_phase(h->Ste, (h->Tm - h->Tc) / (h->Th - h->Tm), ks_kl)
+                   : neumann_lambda(h->Ste);
+    d.t0 = h->Ste > 0.0 ? d.s0 * d.s0 / (4.0 * d.lambda * d.lambda * d.alpha) : 0.0;
+    for (auto &row : h->graphs)
+        for (auto &g : row)
+            if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    h->rb_valid_from = h->rb_next;  // earlier read-backs bound another run
+    h->thw_pending = 0;
+    h->thw_last_prev = 0;
+    const cudaError_t e = initial_state(h);
+    if (e != cudaSuccess) return cuda_err(h, e, "initial state");
+    return seed_readback(h);
 }
 
 LBM_API lbm_status lbm_melt_set_timing(lbm_melt *h, int enable) {
