@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: shifted FP16 storage")
     ap.add_argument("--skip-extra", action="store_true",
                     help="skip the FP16, ensemble and adjoint legs (profiling runs)")
-    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection", "table1"],
+    ap.add_argument("--leg", choices=["precision", "ensemble", "adjoint", "convection", "table1", "solid"],
                     help="run one of the extra legs alone and print its JSON (profiling runs)")
     ap.add_argument("--leg-steps", type=int, default=0, help="steps of that leg (0: its default)")
     ap.add_argument("--dump-dir", default=None, help="directory for the convection leg's final front map (.npy)")
@@ -485,6 +485,66 @@ def table1_leg(n=96):
     return out
 
 
+SOLID_CASE = dict(CASE, Tc=-0.25, Tm=0.0, solid=1, ks_kl=1.0)
+
+
+def solid_leg(steps=200, twin_steps=400):
+    """Heat conduction in a subcooled solid (Eq. 6's k_s term): the 256^3
+    workload with the cold wall at Tc = -0.25 (Tm = 0, k_s = k_l), every node
+    updated each step.  Liquid and all-node MLUPS, the stream-collide's
+    roofline (208 B per liquid node, 56 B per solid node: its 7 energy
+    populations read and written), the step's share outside it, and the
+    error against the FP64 oracle on a 64^3 twin."""
+    import torch
+    import oracle
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    peak, _ = hbm_peak()
+    n = N_EDGE
+    cav = Cavity(n, n, n, stream=stream.cuda_stream, **SOLID_CASE)
+    cav.step(10)
+    cav.sync()
+    S0 = cav.get(T=False, u=False)[2]
+    cav.set_timing(True)
+    cav.kernel_time(reset=True)
+    e0, e1 = _events()
+    e0.record(stream)
+    cav.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k1, nk = cav.kernel_time(reset=True)
+    T, _, S1, lf = cav.get(u=False)
+    cav.close()
+    js = lambda S: float(np.clip(np.ceil(S - 0.5), 0, n).sum())  # noqa: E731
+    n_liq = 0.5 * (js(S0) + js(S1))
+    n_sol = float(n ** 3) - n_liq
+    alg = 208.0 * n_liq + 56.0 * n_sol
+    gbs = alg / (k1 / nk * 1e-3) / 1e9
+    # the 64^3 twin against the oracle
+    m = 64
+    case = dict(SOLID_CASE, s0=0.4 * m)
+    o = oracle.Oracle(m, m, m, **case)
+    g = Cavity(m, m, m, stream=stream.cuda_stream, **case)
+    o.step(twin_steps)
+    g.step(twin_steps)
+    To, _, So, lfo = o.get()
+    Tg, _, Sg, lfg = g.get()
+    o.close()
+    g.close()
+    return {"steps": steps, "ms_per_step": ms / steps, "liquid_mlups": n_liq * steps / (ms * 1e-3) / 1e6,
+            "all_node_mlups": n ** 3 * steps / (ms * 1e-3) / 1e6,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "kernel": "fused stream-collide with conduction in the solid (k_even_cond/k_odd_cond)",
+                         "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1 / nk,
+                         "bytes": "208 per liquid node, 56 per solid node"},
+            "stream_collide_share_of_step": k1 / ms, "min_T": float(T.min()), "liquid_fraction": lf,
+            "twin_error": {"steps": twin_steps, "max_abs_dT": float(np.abs(Tg - To).max()),
+                           "max_abs_dS": float(np.abs(Sg - So).max()), "abs_d_liquid_fraction": abs(lfg - lfo)},
+            "workload": "256^3 heated at y=0, Ra 1e6, Pr 0.02, Ste 0.05, Ma 0.1, cold wall Tc = -0.25 < Tm = 0, "
+                        "k_s = k_l, front at 0.4 H, FP32; twin 64^3 over %d steps" % twin_steps}
+
+
 def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
     """48 seeded cavities of uneven sizes advanced by the persistent kernel
     for the configured 10000 steps (replayed from its captured graph), then
@@ -717,6 +777,7 @@ def run_gpu(args):
         extra["adjoint"] = adjoint_leg()
         extra["convection"] = convection_leg(dump_dir=args.dump_dir)
         extra["table1"] = table1_leg()
+        extra["solid"] = solid_leg()
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -754,7 +815,7 @@ def run_leg(args):
     import torch
     torch.cuda.set_device(0)
     legs = {"precision": precision_leg, "ensemble": ensemble_leg, "adjoint": adjoint_leg,
-            "convection": convection_leg, "table1": table1_leg}
+            "convection": convection_leg, "table1": table1_leg, "solid": solid_leg}
     kw = {"steps": args.leg_steps} if args.leg_steps > 0 and args.leg != "table1" else {}
     if args.leg == "convection":
         kw["dump_dir"] = args.dump_dir

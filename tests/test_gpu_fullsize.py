@@ -1,7 +1,8 @@
 """GPU parity at the full sizes of the benchmark workloads, in the launch
 configuration that bench.py times (default block shapes, the stream-collide
 grid cut at the height bound): the 256^3 side-heated cavity at Ra 1e6 with
-the front at 0.4 H and the 128^3 convection-melting cavity at Ra 1e5.
+the front at 0.4 H (with the solid held at Tm, and with a subcooled,
+conducting solid) and the 128^3 convection-melting cavity at Ra 1e5.
 
 A few steps from the initial state (both AA phases) are compared field by
 field with the FP64 oracle run at the same size; a longer 256^3 run is held
@@ -17,6 +18,10 @@ TOL_T, TOL_LF = 1e-4, 1e-3
 FULL = {
     "256^3 Ra 1e6 front at 0.4 H": (256, dict(face=0, Ra=1e6, Pr=0.02, Ste=0.05, Ma=0.1, s0=0.4 * 256, derive=True)),
     "128^3 Ra 1e5 from s0 = 1": (128, dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)),
+    # the subcooled workload of bench.py's solid leg (heat conduction in the solid)
+    "256^3 Ra 1e6 front at 0.4 H, solid at Tc = -0.25": (
+        256, dict(face=0, Ra=1e6, Pr=0.02, Ste=0.05, Ma=0.1, s0=0.4 * 256, derive=True, Tc=-0.25, solid=1,
+                  ks_kl=1.0)),
 }
 
 
