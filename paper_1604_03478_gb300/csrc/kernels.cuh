@@ -379,6 +379,154 @@ __global__ void __launch_bounds__(128) k_odd_cond(const __grid_constant__ KP p, 
 }
 
 
+// ------------------------------------------- two nodes per thread (FP16)
+// With FP16 storage and an even nx, a thread of the stream-collide takes the
+// nodes x0 = 2k and x0 + 1 of a row.  Their slots of a direction are
+// adjacent and 4-byte aligned (c = index of x0 is even, ld a multiple of 128,
+// and a link offset is even unless the link has an x component), so a pair
+// of liquid nodes moves its populations as half2 words and collides in
+// packed FP32x2 arithmetic (collide2): about half the instructions per node
+// of the one-node kernels, whose FP32 arithmetic, not HBM, bounds them with
+// 2-byte populations.  A pair that meets the interface (or, in the odd step,
+// a wall of the heating axis or of the other in-plane axis) takes the
+// one-node code for each of its nodes.
+// Resident blocks of 128 the pair kernels ask for (the register budget of a
+// thread is 65536 / (128 x this)): 5, 96 registers and under 90 bytes of
+// spills, ran the 256^3 FP16 stream-collide in 0.148 ms against 0.158 ms with
+// 4 (128 registers, no spills) and 0.164 ms with 6 (80 registers, up to
+// 256 bytes of spills).
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 5
+#endif
+
+template <int FACE>
+__device__ __forceinline__ bool k1_pair(const KP &p, const int *jmax, int &x, int &y, int &z) {
+    const int a0 = (int)blockIdx.z * (FACE == 0 ? (int)blockDim.y : 1);
+    if (jmax && a0 >= *jmax + 3) return false;
+    x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (FACE == 0) {
+        y = a0 + (int)threadIdx.y;
+        z = (int)blockIdx.y;
+    } else {
+        y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
+        z = (int)blockIdx.z;
+    }
+    return x < p.nx && y < p.ny;
+}
+
+__device__ __forceinline__ float2 ld_h2(const __half *q) { return __half22float2(*(const __half2 *)q); }
+__device__ __forceinline__ void st_h2(__half *q, float2 v) { __stcs((__half2 *)q, __floats2half2_rn(v.x, v.y)); }
+
+template <int FACE, typename IX>
+__device__ __forceinline__ void even_pair(const KP &p, __half *__restrict__ F, __half *__restrict__ G,
+                                          const int *__restrict__ js, const int *__restrict__ nb,
+                                          const float *__restrict__ gpost, int x, int y, int z) {
+    const int a = axial<FACE>(x, y, z);
+    const int col = column<FACE>(p, x, y, z);  // x + 1 is in column col + 1
+    if (a < __ldg(js + col) && a < __ldg(js + col + 1)) {
+        const IX c = (IX)node_index(p, x, y, z);
+        float2 f[19], g[7];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) f[i] = ld_h2(elem<IX>(F, c, i * p.ld));
+#pragma unroll
+        for (int i = 0; i < 7; ++i) g[i] = ld_h2(elem<IX>(G, c, i * p.ld));
+        collide2(p, f, g);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) st_h2(elem<IX>(F, c, opp(i) * p.ld), f[i]);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) st_h2(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
+    } else {
+        even_node<__half, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
+        even_node<__half, FACE, IX>(p, F, G, js, nb, gpost, x + 1, y, z);
+    }
+}
+
+template <int FACE, typename IX>
+__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_even_pair(const __grid_constant__ KP p, __half *__restrict__ F,
+                                                      __half *__restrict__ G, const int *__restrict__ js,
+                                                      const int *__restrict__ nb, const float *__restrict__ gpost,
+                                                      const int *jmax) {
+    int x, y, z;
+    if (k1_pair<FACE>(p, jmax, x, y, z)) even_pair<FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
+}
+
+// The odd step for a pair: both nodes on the one-node fast path (liquid, off
+// the walls of the heating axis and of the other in-plane axis, one node
+// below the lowest first-solid node of their 3x3 columns).  Links without
+// an x component move as half2 words; the others node by node, with the x
+// walls (x0 = 0 for lane x, x0 + 1 = nx - 1 for lane y) taken as in odd_node.
+template <int FACE, typename IX>
+__device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, __half *__restrict__ F,
+                                         __half *__restrict__ G, const int *__restrict__ js,
+                                         const int *__restrict__ nb, const float *__restrict__ gpost,
+                                         const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
+                                         int y, int z) {
+    const int a = axial<FACE>(x, y, z);
+    const int col = column<FACE>(p, x, y, z);
+    const int q = FACE == 0 ? z : y, nq = FACE == 0 ? p.nz : p.ny;
+    const bool off_qa = q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
+    const bool fast = off_qa && a + 1 < (__ldg(nb + col) >> 16) && a + 1 < (__ldg(nb + col + 1) >> 16);
+    if (!fast) {
+        odd_node<__half, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+        odd_node<__half, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x + 1, y, z);
+        return;
+    }
+    const IX c = (IX)node_index(p, x, y, z), c1 = c + 1;
+    const bool xlo = x == 0, xhi = x + 1 == p.nx - 1;
+    float2 f[19], g[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (ex(i) == 0) {
+            f[i] = ld_h2(elem<IX>(F, c, lk->fin[i]));
+        } else {
+            // across an x wall: bounce-back from the node's own slot i
+            f[i].x = Store<__half>::ld(elem<IX>(F, c, ex(i) > 0 && xlo ? i * p.ld : lk->fin[i]));
+            f[i].y = Store<__half>::ld(elem<IX>(F, c1, ex(i) < 0 && xhi ? i * p.ld : lk->fin[i]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (tx(i) == 0) {
+            g[i] = ld_h2(elem<IX>(G, c, lk->gin[i]));
+        } else {
+            g[i].x = Store<__half>::ld(elem<IX>(G, c, tx(i) > 0 && xlo ? i * p.ld : lk->gin[i]));
+            g[i].y = Store<__half>::ld(elem<IX>(G, c1, tx(i) < 0 && xhi ? i * p.ld : lk->gin[i]));
+        }
+    }
+    collide2(p, f, g);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (ex(i) == 0) {
+            st_h2(elem<IX>(F, c, lk->fout[i]), f[i]);
+        } else {
+            // towards an x wall: stays in the node's slot opp(i)
+            Store<__half>::st_stream(elem<IX>(F, c, ex(i) < 0 && xlo ? opp(i) * p.ld : lk->fout[i]), f[i].x);
+            Store<__half>::st_stream(elem<IX>(F, c1, ex(i) > 0 && xhi ? opp(i) * p.ld : lk->fout[i]), f[i].y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (tx(i) == 0) {
+            st_h2(elem<IX>(G, c, lk->gout[i]), g[i]);
+        } else {
+            Store<__half>::st_stream(elem<IX>(G, c, tx(i) < 0 && xlo ? opp7(i) * p.ld : lk->gout[i]), g[i].x);
+            Store<__half>::st_stream(elem<IX>(G, c1, tx(i) > 0 && xhi ? opp7(i) * p.ld : lk->gout[i]), g[i].y);
+        }
+    }
+}
+
+template <int FACE, typename IX>
+__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_odd_pair(const __grid_constant__ KP p, __half *__restrict__ F,
+                                                     __half *__restrict__ G, const int *__restrict__ js,
+                                                     const int *__restrict__ nb, const float *__restrict__ gpost,
+                                                     const float *__restrict__ thw_rd,
+                                                     const float *__restrict__ thw_wr,
+                                                     const __grid_constant__ Links lk, const int *jmax) {
+    int x, y, z;
+    if (k1_pair<FACE>(p, jmax, x, y, z)) odd_pair<FACE, IX>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+}
+
+
 // -------------------------------------------------- state gathers (natural)
 // Shifted pre-collision g of node (x,y,z).  In flight: pull from the
 // neighbours' slots (walls by their rules with wall field thw); natural:

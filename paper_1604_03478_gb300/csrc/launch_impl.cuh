@@ -20,6 +20,27 @@ static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, d
     }
 }
 
+#ifndef LBM_PAIR_ODD_IX
+#define LBM_PAIR_ODD_IX unsigned
+#endif
+// FP16 storage with an even nx: two nodes per thread (k_even_pair /
+// k_odd_pair), the grid's x extent covering nx / 2 threads.
+template <typename IXE, typename IXO>
+static void launch_sc_pair(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
+    const int *jm = p.skip_deep ? b.jmax : nullptr;
+    __half *F = (__half *)b.F, *G = (__half *)b.G;
+    KP half_x = p;
+    half_x.nx = p.nx / 2;
+    dim3 grd = k1_grid(half_x, blk, face, b.k1_height);
+    if (face == 0) {
+        if (odd) k_odd_pair<0, IXO><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else k_even_pair<0, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+    } else {
+        if (odd) k_odd_pair<1, IXO><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else k_even_pair<1, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+    }
+}
+
 // The even step indexes in 32 bits whenever every index of the 19 direction
 // arrays of F fits (19 ld < 2^32: cavities up to about 2.2e8 nodes), else in
 // 64 bits (FP16 storage 2% faster at 256^3; the odd step ran slower with
@@ -27,6 +48,13 @@ static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, d
 template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
     if (p.cond) return LaunchCond<ST>::stream_collide(p, face, odd, b, blk, st);
+    if constexpr (sizeof(ST) == 2) {
+        if (p.nx % 2 == 0) {
+            if (19LL * p.ld < (1LL << 32)) launch_sc_pair<unsigned, LBM_PAIR_ODD_IX>(p, face, odd, b, blk, st);
+            else launch_sc_pair<long long, long long>(p, face, odd, b, blk, st);
+            return cudaGetLastError();
+        }
+    }
     const dim3 grd = k1_grid(p, blk, face, b.k1_height);
     if (19LL * p.ld < (1LL << 32)) launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
     else launch_sc<ST, long long>(p, face, odd, b, grd, blk, st);

@@ -376,6 +376,102 @@ __host__ __device__ __forceinline__ void add_back_shared(float (&f)[19], const f
     f[16] += E16 + O16; f[17] += E16 - O16;
 }
 
+// --------------------------------------------------- two-lane arithmetic
+// Two nodes per thread (lane x and lane y of a float2): every operation is
+// one packed FP32x2 instruction of sm_100 and later (add/mul/fma .f32x2,
+// each lane rounded to nearest like the scalar FP32 instruction), so two
+// nodes cost about the arithmetic instructions of one.  The host versions
+// (for checks on the CPU) do the same lane by lane.
+__host__ __device__ __forceinline__ float2 v2(float s) { return make_float2(s, s); }
+__host__ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    return __fmul2_rn(a, b);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+// a - b as fma(b, -1, a): one rounding, the exact difference rounded
+__host__ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, v2(-1.0f), a); }
+// s b + c and s b with a scalar (uniform) coefficient
+__host__ __device__ __forceinline__ float2 sfma2(float s, float2 b, float2 c) { return fma2(v2(s), b, c); }
+__host__ __device__ __forceinline__ float2 smul2(float s, float2 b) { return mul2(v2(s), b); }
+
+// moments_shared for two nodes.
+__host__ __device__ __forceinline__ void moments_shared2(float2 f0, const float2 (&S)[9], const float2 (&D)[9],
+                                                         float2 (&m)[19]) {
+    const float2 Sx = S[0], Sy = S[1], Sz = S[2], S7 = S[3], S8 = S[4], S11 = S[5], S12 = S[6], S15 = S[7],
+                 S16 = S[8];
+    const float2 Dx = D[0], Dy = D[1], Dz = D[2], D7 = D[3], D8 = D[4], D11 = D[5], D12 = D[6], D15 = D[7],
+                 D16 = D[8];
+    const float2 Sxy = add2(S7, S8), Sxz = add2(S11, S12), Syz = add2(S15, S16);
+    const float2 Sax = add2(add2(Sx, Sy), Sz), Sdg = add2(add2(Sxy, Sxz), Syz);
+    m[0] = add2(add2(f0, Sax), Sdg);
+    m[1] = sfma2(8.0f, Sdg, sfma2(-11.0f, Sax, smul2(-30.0f, f0)));
+    m[2] = sfma2(-4.0f, Sax, sfma2(12.0f, f0, Sdg));
+    const float2 a9 = sub2(smul2(2.0f, Sx), add2(Sy, Sz));
+    const float2 d9 = sfma2(-2.0f, Syz, add2(Sxy, Sxz));
+    m[9] = add2(a9, d9);
+    m[10] = sfma2(-2.0f, a9, d9);
+    const float2 a11 = sub2(Sy, Sz), d11 = sub2(Sxy, Sxz);
+    m[11] = add2(a11, d11);
+    m[12] = sfma2(-2.0f, a11, d11);
+    m[13] = sub2(S7, S8);
+    m[14] = sub2(S15, S16);
+    m[15] = sub2(S11, S12);
+    const float2 A = sub2(D7, D8), B = sub2(D11, D12), Xd = add2(A, B);
+    m[3] = add2(Dx, Xd);
+    m[4] = sfma2(-4.0f, Dx, Xd);
+    m[16] = sub2(A, B);
+    const float2 C = add2(D7, D8), E = sub2(D15, D16), Yd = add2(C, E);
+    m[5] = add2(Dy, Yd);
+    m[6] = sfma2(-4.0f, Dy, Yd);
+    m[17] = sub2(E, C);
+    const float2 G = add2(D11, D12), H = add2(D15, D16), Zd = add2(G, H);
+    m[7] = add2(Dz, Zd);
+    m[8] = sfma2(-4.0f, Dz, Zd);
+    m[18] = sub2(G, H);
+}
+
+// add_back_shared for two nodes (c[0] = c[3] = c[5] = 0).
+__host__ __device__ __forceinline__ void add_back_shared2(float2 (&f)[19], const float2 (&c)[19]) {
+    f[0] = sfma2(12.0f, c[2], sfma2(-30.0f, c[1], f[0]));
+    const float2 Kax = sfma2(-4.0f, c[2], smul2(-11.0f, c[1])), Kdg = sfma2(8.0f, c[1], c[2]);
+    const float2 b1 = sfma2(-2.0f, c[10], c[9]), b2 = add2(c[9], c[10]);
+    const float2 b3 = sfma2(-2.0f, c[12], c[11]), b4 = add2(c[11], c[12]);
+    const float2 Ex = sfma2(2.0f, b1, Kax), Ky = sub2(Kax, b1), Ey = add2(Ky, b3), Ez = sub2(Ky, b3);
+    const float2 K1 = add2(Kdg, b2), K2 = add2(K1, b4), K3 = sub2(K1, b4), K4 = sfma2(-2.0f, b2, Kdg);
+    const float2 E7 = add2(K2, c[13]), E8 = sub2(K2, c[13]), E11 = add2(K3, c[15]), E12 = sub2(K3, c[15]);
+    const float2 E15 = add2(K4, c[14]), E16 = sub2(K4, c[14]);
+    const float2 Ox = smul2(-4.0f, c[4]), Oy = smul2(-4.0f, c[6]), Oz = sfma2(-4.0f, c[8], c[7]);
+    const float2 P = add2(c[4], c[16]), Q = sub2(c[6], c[17]), Pp = sub2(c[4], c[16]), Qp = add2(c[6], c[17]);
+    const float2 c78 = add2(c[7], c[8]), R = add2(c78, c[18]), Rp = sub2(c78, c[18]);
+    const float2 O7 = add2(P, Q), O8 = sub2(Q, P), O11 = add2(Pp, R), O12 = sub2(R, Pp), O15 = add2(Qp, Rp),
+                 O16 = sub2(Rp, Qp);
+    f[1] = add2(f[1], add2(Ex, Ox));    f[2] = add2(f[2], sub2(Ex, Ox));
+    f[3] = add2(f[3], add2(Ey, Oy));    f[4] = add2(f[4], sub2(Ey, Oy));
+    f[5] = add2(f[5], add2(Ez, Oz));    f[6] = add2(f[6], sub2(Ez, Oz));
+    f[7] = add2(f[7], add2(E7, O7));    f[10] = add2(f[10], sub2(E7, O7));
+    f[8] = add2(f[8], add2(E8, O8));    f[9] = add2(f[9], sub2(E8, O8));
+    f[11] = add2(f[11], add2(E11, O11)); f[14] = add2(f[14], sub2(E11, O11));
+    f[12] = add2(f[12], add2(E12, O12)); f[13] = add2(f[13], sub2(E12, O12));
+    f[15] = add2(f[15], add2(E15, O15)); f[18] = add2(f[18], sub2(E15, O15));
+    f[16] = add2(f[16], add2(E16, O16)); f[17] = add2(f[17], sub2(E16, O16));
+}
+
 // -------------------------------------------------------------- collision
 // One liquid node: shifted populations in, shifted post-collision out.
 //   T = Ts + sum gh;  F = g beta (T - Tm) z-hat (Boussinesq, gravity -z);
@@ -441,6 +537,91 @@ __device__ __forceinline__ void collide(const KP &p, float (&f)[19], float (&g)[
     cn[6] = -p.s_g5 * n6 * i6;
     add_back7<0>(g, cn);
     if (uout) { uout[0] = ux; uout[1] = uy; uout[2] = uz; }
+}
+
+// collide for two liquid nodes at once (lane x and lane y), packed FP32x2
+// arithmetic: the same equations, with each row's rate and inverse norm
+// folded into uniform coefficients (c[k] = d[k] / |row k|^2 formed
+// directly).
+__device__ __forceinline__ void collide2(const KP &p, float2 (&f)[19], float2 (&g)[7]) {
+    const float2 g12 = add2(g[1], g[2]), g34 = add2(g[3], g[4]), g56 = add2(g[5], g[6]);
+    const float2 Th = add2(g[0], add2(g12, add2(g34, g56)));      // T - Ts
+    const float2 T = add2(Th, v2(p.Ts));
+    const float2 Fz = sfma2(p.gbeta, Th, v2(-p.gbeta * p.dTms));  // g beta (T - Tm)
+    float2 m[19], S[9], D[9];
+#pragma unroll
+    for (int P = 0; P < 9; ++P) {
+        S[P] = add2(f[pf(P)], f[opp(pf(P))]);
+        D[P] = sub2(f[pf(P)], f[opp(pf(P))]);
+    }
+    moments_shared2(f[0], S, D, m);
+    const float2 rho_h = m[0];
+    const float2 ux = m[3], uy = m[5], uz = sfma2(0.5f, Fz, m[7]);
+    const float2 ux2 = mul2(ux, ux), uy2 = mul2(uy, uy), uz2 = mul2(uz, uz);
+    const float2 uu = add2(ux2, add2(uy2, uz2));
+    const float2 uzF = mul2(uz, Fz);
+    const float2 pxx = sub2(smul2(3.0f, ux2), uu);  // 2 ux^2 - uy^2 - uz^2
+    const float2 pww = sub2(uy2, uz2);
+    constexpr float n1 = 1.0f / (float)mnorm(1), n2 = 1.0f / (float)mnorm(2), n4 = 1.0f / (float)mnorm(4);
+    constexpr float n7 = 1.0f / (float)mnorm(7), n9 = 1.0f / (float)mnorm(9), n10 = 1.0f / (float)mnorm(10);
+    constexpr float n11 = 1.0f / (float)mnorm(11), n12 = 1.0f / (float)mnorm(12), n13 = 1.0f / (float)mnorm(13);
+    constexpr float n16 = 1.0f / (float)mnorm(16);
+    const float se = p.s_e, sps = p.s_eps, sq = p.s_q, snu = p.s_nu, spi = p.s_pi, sm = p.s_m;
+    float2 c[19];
+    // d1 = -s_e (m1 + 11 rho - 19 u^2) + (1 - s_e/2) 38 uz F
+    c[1] = sfma2(-se * n1, m[1], sfma2(-11.0f * se * n1, rho_h,
+                 sfma2(19.0f * se * n1, uu, smul2(38.0f * (1.0f - 0.5f * se) * n1, uzF))));
+    // d2 = -s_eps (m2 - 3 rho + 5.5 u^2) - 11 (1 - s_eps/2) uz F
+    c[2] = sfma2(-sps * n2, m[2], sfma2(3.0f * sps * n2, rho_h,
+                 sfma2(-5.5f * sps * n2, uu, smul2(-11.0f * (1.0f - 0.5f * sps) * n2, uzF))));
+    c[0] = v2(0.0f);
+    c[3] = v2(0.0f);
+    c[5] = v2(0.0f);
+    // d4, d6 = -s_q (m + 2/3 u);  d8 adds -(2/3)(1 - s_q/2) F
+    c[4] = sfma2(-sq * n4, m[4], smul2(-(2.0f / 3.0f) * sq * n4, ux));
+    c[6] = sfma2(-sq * n4, m[6], smul2(-(2.0f / 3.0f) * sq * n4, uy));
+    c[7] = smul2(n7, Fz);
+    c[8] = sfma2(-sq * n4, m[8], sfma2(-(2.0f / 3.0f) * sq * n4, uz,
+                 smul2(-(2.0f / 3.0f) * (1.0f - 0.5f * sq) * n4, Fz)));
+    // viscous rows
+    const float knu = 1.0f - 0.5f * snu, kpi = 1.0f - 0.5f * spi;
+    c[9] = sfma2(-snu * n9, sub2(m[9], pxx), smul2(-2.0f * knu * n9, uzF));
+    c[10] = sfma2(-spi * n10, sfma2(0.5f, pxx, m[10]), smul2(kpi * n10, uzF));
+    c[11] = sfma2(-snu * n11, sub2(m[11], pww), smul2(-2.0f * knu * n11, uzF));
+    c[12] = sfma2(-spi * n12, sfma2(0.5f, pww, m[12]), smul2(kpi * n12, uzF));
+    c[13] = smul2(-snu * n13, sub2(m[13], mul2(ux, uy)));
+    c[14] = sfma2(-snu * n13, sub2(m[14], mul2(uy, uz)), smul2(knu * n13, mul2(uy, Fz)));
+    c[15] = sfma2(-snu * n13, sub2(m[15], mul2(ux, uz)), smul2(knu * n13, mul2(ux, Fz)));
+    c[16] = smul2(-sm * n16, m[16]);
+    c[17] = smul2(-sm * n16, m[17]);
+    c[18] = smul2(-sm * n16, m[18]);
+    add_back_shared2(f, c);
+
+    // D3Q7: n* - n = -Q (n - n^eq), n^eq = (T, u T, 3T/4, 0, 0)
+    constexpr float i1 = 1.0f / (float)nnorm(1), i4 = 1.0f / (float)nnorm(4);
+    constexpr float i5 = 1.0f / (float)nnorm(5), i6 = 1.0f / (float)nnorm(6);
+    const float sa = p.s_alpha, s4 = p.s_g4, s5 = p.s_g5;
+    float2 cn[7];
+    cn[1] = sfma2(-sa * i1, sub2(g[1], g[2]), smul2(sa * i1, mul2(ux, T)));
+    cn[2] = sfma2(-sa * i1, sub2(g[3], g[4]), smul2(sa * i1, mul2(uy, T)));
+    cn[3] = sfma2(-sa * i1, sub2(g[5], g[6]), smul2(sa * i1, mul2(uz, T)));
+    // n4 = 6 g0 - (g1 + ... + g6) = 7 g0 - Th; n4^eq (shifted) = 3 Th / 4;
+    // mc4 = -cn[4]
+    const float2 mc4 = smul2(s4 * i4, sfma2(7.0f, g[0], smul2(-1.75f, Th)));
+    cn[5] = smul2(-s5 * i5, sub2(smul2(2.0f, g12), add2(g34, g56)));
+    cn[6] = smul2(-s5 * i6, sub2(g34, g56));
+    // g += N^T cn (row 0 carries nothing): rows 4 and 5 weigh the rest
+    // population 6, 0, the x links -1, 2, the y and z links -1, -1
+    g[0] = sfma2(-6.0f, mc4, g[0]);
+    const float2 ex4 = sfma2(2.0f, cn[5], mc4);
+    const float2 yz4 = sub2(mc4, cn[5]);
+    g[1] = add2(g[1], add2(ex4, cn[1]));
+    g[2] = add2(g[2], sub2(ex4, cn[1]));
+    const float2 ey = add2(yz4, cn[6]), ez = sub2(yz4, cn[6]);
+    g[3] = add2(g[3], add2(ey, cn[2]));
+    g[4] = add2(g[4], sub2(ey, cn[2]));
+    g[5] = add2(g[5], add2(ez, cn[3]));
+    g[6] = add2(g[6], sub2(ez, cn[3]));
 }
 
 // Heat conduction in a solid node: the D3Q7 collision of Eq. 4 at u = 0 with
