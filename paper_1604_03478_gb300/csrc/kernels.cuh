@@ -398,6 +398,12 @@ __global__ void __launch_bounds__(128) k_odd_cond(const __grid_constant__ KP p, 
 #ifndef LBM_PAIR_MIN_BLOCKS
 #define LBM_PAIR_MIN_BLOCKS 5
 #endif
+#ifndef LBM_PAIR_MIN_BLOCKS_F32
+#define LBM_PAIR_MIN_BLOCKS_F32 5
+#endif
+template <typename ST> constexpr int pair_min_blocks() {
+    return sizeof(ST) == 2 ? LBM_PAIR_MIN_BLOCKS : LBM_PAIR_MIN_BLOCKS_F32;
+}
 
 template <int FACE>
 __device__ __forceinline__ bool k1_pair(const KP &p, const int *jmax, int &x, int &y, int &z) {
@@ -414,11 +420,14 @@ __device__ __forceinline__ bool k1_pair(const KP &p, const int *jmax, int &x, in
     return x < p.nx && y < p.ny;
 }
 
-__device__ __forceinline__ float2 ld_h2(const __half *q) { return __half22float2(*(const __half2 *)q); }
-__device__ __forceinline__ void st_h2(__half *q, float2 v) { __stcs((__half2 *)q, __floats2half2_rn(v.x, v.y)); }
+// The two adjacent populations of a pair (an aligned half2 or float2 word).
+__device__ __forceinline__ float2 ld_pair(const __half *q) { return __half22float2(*(const __half2 *)q); }
+__device__ __forceinline__ float2 ld_pair(const float *q) { return *(const float2 *)q; }
+__device__ __forceinline__ void st_pair(__half *q, float2 v) { __stcs((__half2 *)q, __floats2half2_rn(v.x, v.y)); }
+__device__ __forceinline__ void st_pair(float *q, float2 v) { __stcs((float2 *)q, v); }
 
-template <int FACE, typename IX>
-__device__ __forceinline__ void even_pair(const KP &p, __half *__restrict__ F, __half *__restrict__ G,
+template <typename ST, int FACE, typename IX>
+__device__ __forceinline__ void even_pair(const KP &p, ST *__restrict__ F, ST *__restrict__ G,
                                           const int *__restrict__ js, const int *__restrict__ nb,
                                           const float *__restrict__ gpost, int x, int y, int z) {
     const int a = axial<FACE>(x, y, z);
@@ -427,27 +436,27 @@ __device__ __forceinline__ void even_pair(const KP &p, __half *__restrict__ F, _
         const IX c = (IX)node_index(p, x, y, z);
         float2 f[19], g[7];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = ld_h2(elem<IX>(F, c, i * p.ld));
+        for (int i = 0; i < 19; ++i) f[i] = ld_pair(elem<IX>(F, c, i * p.ld));
 #pragma unroll
-        for (int i = 0; i < 7; ++i) g[i] = ld_h2(elem<IX>(G, c, i * p.ld));
+        for (int i = 0; i < 7; ++i) g[i] = ld_pair(elem<IX>(G, c, i * p.ld));
         collide2(p, f, g);
 #pragma unroll
-        for (int i = 0; i < 19; ++i) st_h2(elem<IX>(F, c, opp(i) * p.ld), f[i]);
+        for (int i = 0; i < 19; ++i) st_pair(elem<IX>(F, c, opp(i) * p.ld), f[i]);
 #pragma unroll
-        for (int i = 0; i < 7; ++i) st_h2(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
+        for (int i = 0; i < 7; ++i) st_pair(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
     } else {
-        even_node<__half, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
-        even_node<__half, FACE, IX>(p, F, G, js, nb, gpost, x + 1, y, z);
+        even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
+        even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x + 1, y, z);
     }
 }
 
-template <int FACE, typename IX>
-__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_even_pair(const __grid_constant__ KP p, __half *__restrict__ F,
-                                                      __half *__restrict__ G, const int *__restrict__ js,
+template <typename ST, int FACE, typename IX>
+__global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_even_pair(const __grid_constant__ KP p, ST *__restrict__ F,
+                                                      ST *__restrict__ G, const int *__restrict__ js,
                                                       const int *__restrict__ nb, const float *__restrict__ gpost,
                                                       const int *jmax) {
     int x, y, z;
-    if (k1_pair<FACE>(p, jmax, x, y, z)) even_pair<FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
+    if (k1_pair<FACE>(p, jmax, x, y, z)) even_pair<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
 }
 
 // The odd step for a pair: both nodes on the one-node fast path (liquid, off
@@ -455,9 +464,9 @@ __global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_even_pair(const __
 // below the lowest first-solid node of their 3x3 columns).  Links without
 // an x component move as half2 words; the others node by node, with the x
 // walls (x0 = 0 for lane x, x0 + 1 = nx - 1 for lane y) taken as in odd_node.
-template <int FACE, typename IX>
-__device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, __half *__restrict__ F,
-                                         __half *__restrict__ G, const int *__restrict__ js,
+template <typename ST, int FACE, typename IX>
+__device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, ST *__restrict__ F,
+                                         ST *__restrict__ G, const int *__restrict__ js,
                                          const int *__restrict__ nb, const float *__restrict__ gpost,
                                          const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
                                          int y, int z) {
@@ -467,8 +476,8 @@ __device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, __half *_
     const bool off_qa = q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
     const bool fast = off_qa && a + 1 < (__ldg(nb + col) >> 16) && a + 1 < (__ldg(nb + col + 1) >> 16);
     if (!fast) {
-        odd_node<__half, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
-        odd_node<__half, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x + 1, y, z);
+        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x + 1, y, z);
         return;
     }
     const IX c = (IX)node_index(p, x, y, z), c1 = c + 1;
@@ -477,53 +486,53 @@ __device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, __half *_
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (ex(i) == 0) {
-            f[i] = ld_h2(elem<IX>(F, c, lk->fin[i]));
+            f[i] = ld_pair(elem<IX>(F, c, lk->fin[i]));
         } else {
             // across an x wall: bounce-back from the node's own slot i
-            f[i].x = Store<__half>::ld(elem<IX>(F, c, ex(i) > 0 && xlo ? i * p.ld : lk->fin[i]));
-            f[i].y = Store<__half>::ld(elem<IX>(F, c1, ex(i) < 0 && xhi ? i * p.ld : lk->fin[i]));
+            f[i].x = Store<ST>::ld(elem<IX>(F, c, ex(i) > 0 && xlo ? i * p.ld : lk->fin[i]));
+            f[i].y = Store<ST>::ld(elem<IX>(F, c1, ex(i) < 0 && xhi ? i * p.ld : lk->fin[i]));
         }
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         if (tx(i) == 0) {
-            g[i] = ld_h2(elem<IX>(G, c, lk->gin[i]));
+            g[i] = ld_pair(elem<IX>(G, c, lk->gin[i]));
         } else {
-            g[i].x = Store<__half>::ld(elem<IX>(G, c, tx(i) > 0 && xlo ? i * p.ld : lk->gin[i]));
-            g[i].y = Store<__half>::ld(elem<IX>(G, c1, tx(i) < 0 && xhi ? i * p.ld : lk->gin[i]));
+            g[i].x = Store<ST>::ld(elem<IX>(G, c, tx(i) > 0 && xlo ? i * p.ld : lk->gin[i]));
+            g[i].y = Store<ST>::ld(elem<IX>(G, c1, tx(i) < 0 && xhi ? i * p.ld : lk->gin[i]));
         }
     }
     collide2(p, f, g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (ex(i) == 0) {
-            st_h2(elem<IX>(F, c, lk->fout[i]), f[i]);
+            st_pair(elem<IX>(F, c, lk->fout[i]), f[i]);
         } else {
             // towards an x wall: stays in the node's slot opp(i)
-            Store<__half>::st_stream(elem<IX>(F, c, ex(i) < 0 && xlo ? opp(i) * p.ld : lk->fout[i]), f[i].x);
-            Store<__half>::st_stream(elem<IX>(F, c1, ex(i) > 0 && xhi ? opp(i) * p.ld : lk->fout[i]), f[i].y);
+            Store<ST>::st_stream(elem<IX>(F, c, ex(i) < 0 && xlo ? opp(i) * p.ld : lk->fout[i]), f[i].x);
+            Store<ST>::st_stream(elem<IX>(F, c1, ex(i) > 0 && xhi ? opp(i) * p.ld : lk->fout[i]), f[i].y);
         }
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         if (tx(i) == 0) {
-            st_h2(elem<IX>(G, c, lk->gout[i]), g[i]);
+            st_pair(elem<IX>(G, c, lk->gout[i]), g[i]);
         } else {
-            Store<__half>::st_stream(elem<IX>(G, c, tx(i) < 0 && xlo ? opp7(i) * p.ld : lk->gout[i]), g[i].x);
-            Store<__half>::st_stream(elem<IX>(G, c1, tx(i) > 0 && xhi ? opp7(i) * p.ld : lk->gout[i]), g[i].y);
+            Store<ST>::st_stream(elem<IX>(G, c, tx(i) < 0 && xlo ? opp7(i) * p.ld : lk->gout[i]), g[i].x);
+            Store<ST>::st_stream(elem<IX>(G, c1, tx(i) > 0 && xhi ? opp7(i) * p.ld : lk->gout[i]), g[i].y);
         }
     }
 }
 
-template <int FACE, typename IX>
-__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_odd_pair(const __grid_constant__ KP p, __half *__restrict__ F,
-                                                     __half *__restrict__ G, const int *__restrict__ js,
+template <typename ST, int FACE, typename IX>
+__global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_odd_pair(const __grid_constant__ KP p, ST *__restrict__ F,
+                                                     ST *__restrict__ G, const int *__restrict__ js,
                                                      const int *__restrict__ nb, const float *__restrict__ gpost,
                                                      const float *__restrict__ thw_rd,
                                                      const float *__restrict__ thw_wr,
                                                      const __grid_constant__ Links lk, const int *jmax) {
     int x, y, z;
-    if (k1_pair<FACE>(p, jmax, x, y, z)) odd_pair<FACE, IX>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+    if (k1_pair<FACE>(p, jmax, x, y, z)) odd_pair<ST, FACE, IX>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
 }
 
 

@@ -191,7 +191,9 @@ def test_held_front_gives_linear_profiles(lib, kappa):
 def test_no_subcooling_is_the_held_solid_method(lib, face):
     """Tc = Tm: the solid stays at Tm exactly, so until the first node
     changes phase the conduction kernels give the held-solid method's
-    results bit for bit (FP32 storage)."""
+    results (FP32 storage).  The held-solid kernels collide two nodes per
+    thread in packed FP32x2 arithmetic and the conduction kernels one, so
+    the two agree to FP32 rounding rather than bit for bit."""
     kw = dict(face=face, Ra=5e4, Pr=0.02, Ste=0.1, Ma=0.1, s0=3.0, derive=True, Tc=0.0, Tm=0.0)
     shape = (12, 16, 10) if face == 0 else (12, 10, 16)
     a = lib(*shape, **kw)
@@ -201,9 +203,12 @@ def test_no_subcooling_is_the_held_solid_method(lib, face):
     Ta, ua, Sa, _ = a.get()
     Tb, ub, Sb, _ = b.get()
     assert Sa.min() > 3.2 and Sa.max() < 3.5  # moved, no flip yet
-    np.testing.assert_array_equal(Sa, Sb)
-    np.testing.assert_array_equal(Ta, Tb)
-    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_allclose(Sa, Sb, atol=1e-7, rtol=0)  # 1.3e-8 measured
+    np.testing.assert_allclose(Ta, Tb, atol=1e-6, rtol=0)
+    np.testing.assert_allclose(ua, ub, atol=1e-7, rtol=0)
+    # the solid stays at Tm exactly in both
+    solid = Ta == 0.0
+    assert solid.sum() > 0 and np.all(Tb[solid] == 0.0)
 
 
 def test_fp16_storage_error(lib, orc):
