@@ -248,6 +248,18 @@ lbm_status lbm_melt_kernel_time(lbm_melt *h, double *ms, long long *launches, in
    (lbm_melt_set_timing) run step by step.  steps in [0, 256]. */
 lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps);
 
+/* Nodes per thread of the stream-collide (the same method and results up to
+   FP32 rounding): -1 (default) chooses two for cavities above 160^3 nodes
+   with an even nx and one otherwise; 0 one node per thread; 1 two nodes per
+   thread (x-adjacent nodes as the two lanes of packed FP32x2 arithmetic,
+   their populations moved as float2/half2 words where aligned; needs an
+   even nx, else LBM_EINVAL).  With heat conduction in the solid the
+   stream-collide takes one node per thread whatever the mode.  Two nodes
+   per thread pay about half the instructions per node and win where the
+   grid is large; small grids with a thin liquid layer are latency bound
+   and run faster with one. */
+lbm_status lbm_melt_set_node_pairs(lbm_melt *h, int mode);
+
 /* Heat conduction in the solid: the k_s dT_s/da term of Eq. 6, for a cold
    wall below the melting point (Tc < Tm, a subcooled solid; the paper
    solves only zero subcooling, where the solid stays at Tm and the term

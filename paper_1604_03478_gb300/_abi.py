@@ -81,6 +81,7 @@ def load() -> C.CDLL:
         "lbm_melt_set_timing": (C.c_int, [vp, C.c_int]),
         "lbm_melt_set_graph_steps": (C.c_int, [vp, C.c_int]),
         "lbm_melt_set_solid_conduction": (C.c_int, [vp, C.c_double]),
+        "lbm_melt_set_node_pairs": (C.c_int, [vp, C.c_int]),
         "lbm_melt_set_launch": (C.c_int, [vp, C.c_int, C.c_int]),
         "lbm_melt_kernel_time": (C.c_int, [vp, dp, C.POINTER(C.c_longlong), C.c_int]),
         "lbm_melt_last_error": (C.c_char_p, [vp]),

@@ -208,6 +208,11 @@ class Cavity:
     def set_timing(self, on=True):
         self._check(_abi.load().lbm_melt_set_timing(self._h, 1 if on else 0))
 
+    def set_node_pairs(self, mode):
+        """Nodes per thread of the stream-collide: -1 choose, 0 one, 1 two
+        (lbm_melt_set_node_pairs)."""
+        self._check(_abi.load().lbm_melt_set_node_pairs(self._h, int(mode)))
+
     def set_solid_conduction(self, ks_kl):
         """Heat conduction in the solid with k_s / k_l = ks_kl (0: off);
         before the first step, re-initialises the state."""

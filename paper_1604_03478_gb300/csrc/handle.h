@@ -81,6 +81,9 @@ struct lbm_melt {
     // starting (cur, inflight) phase; each records the stream-collide grid
     // height and block shape it was captured with.
     int graph_steps;
+    // Nodes per thread of the stream-collide: -1 chooses (two for cavities
+    // above 160^3 with an even nx, one otherwise), 0 one, 1 two (even nx).
+    int pairs_mode;
     cudaStream_t cap_stream;     // private stream the graphs are captured on
     struct StepGraph {
         cudaGraphExec_t exec;

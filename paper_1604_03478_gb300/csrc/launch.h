@@ -27,6 +27,7 @@ struct Bufs {
     double *nu;                  // per-column Nusselt numbers (ncols)
     double nu_scale;             // H / (alpha (Th - Tm))
     float *spost;                // solid-side ghost populations, 7 x ncols (heat conduction in the solid)
+    int pairs;                   // stream-collide with two nodes per thread (even nx)
 };
 
 // The stream-collide and front kernels with heat conduction in the solid

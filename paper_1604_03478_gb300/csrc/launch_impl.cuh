@@ -20,11 +20,6 @@ static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, d
     }
 }
 
-// FP32 storage takes the pair kernels too (256^3: 0.2245 against 0.234 ms
-// per stream-collide launch, 0.914 against 0.877 of the measured peak).
-#ifndef LBM_PAIR_F32
-#define LBM_PAIR_F32 1
-#endif
 #ifndef LBM_PAIR_ODD_IX
 #define LBM_PAIR_ODD_IX unsigned
 #endif
@@ -53,12 +48,10 @@ static void launch_sc_pair(const KP &p, int face, int odd, const Bufs &b, dim3 b
 template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
     if (p.cond) return LaunchCond<ST>::stream_collide(p, face, odd, b, blk, st);
-    if constexpr (sizeof(ST) == 2 || LBM_PAIR_F32) {
-        if (p.nx % 2 == 0) {
-            if (19LL * p.ld < (1LL << 32)) launch_sc_pair<ST, unsigned, LBM_PAIR_ODD_IX>(p, face, odd, b, blk, st);
-            else launch_sc_pair<ST, long long, long long>(p, face, odd, b, blk, st);
-            return cudaGetLastError();
-        }
+    if (b.pairs && p.nx % 2 == 0) {
+        if (19LL * p.ld < (1LL << 32)) launch_sc_pair<ST, unsigned, LBM_PAIR_ODD_IX>(p, face, odd, b, blk, st);
+        else launch_sc_pair<ST, long long, long long>(p, face, odd, b, blk, st);
+        return cudaGetLastError();
     }
     const dim3 grd = k1_grid(p, blk, face, b.k1_height);
     if (19LL * p.ld < (1LL << 32)) launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
