@@ -620,32 +620,56 @@ def adjoint_leg(steps=4000, n=96):
     case = dict(face=0, Ra=1e5, Pr=0.02, Ste=0.1, Ma=0.1, s0=1.0, derive=True)
     wall = (1.0 + inputs.gaussian_field(n * n, 0.01, 5)).astype(np.float32)
     res = {}
-    for mode in ("plain", "tape"):
-        cav = Cavity(n, n, n, stream=stream.cuda_stream, **case)
-        cav.set_hot_wall(wall)
+    seed = np.full(n * n, 1.0 / (n * n * n))
+
+    def gradient(cav, key):
         e0, e1 = _events()
         torch.cuda.synchronize()
         e0.record(stream)
-        if mode == "plain":
-            cav.step(steps)
-        else:
-            cav.tape_forward(steps)
+        cav.tape_forward(steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        res[mode] = e0.elapsed_time(e1)
-        if mode == "tape":
-            seed = np.full(cav.ncols, 1.0 / (cav.H * cav.ncols))
-            t0 = time.perf_counter()
-            dth, par = cav.tape_backward(seed)
-            res["backward"] = (time.perf_counter() - t0) * 1e3
-            res["dL_dRa"] = par["Ra"]
-            res["grad_norm_wall"] = float(np.linalg.norm(dth))
-            res["dL_dv1"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 7))
-            res["dL_dv2"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 8))
-        cav.close()
+        res["tape" + key] = e0.elapsed_time(e1)
+        t0 = time.perf_counter()
+        dth, par = cav.tape_backward(seed)
+        res["backward" + key] = (time.perf_counter() - t0) * 1e3
+        return dth, par
+
+    # the plain forward run
+    cav = Cavity(n, n, n, stream=stream.cuda_stream, **case)
+    cav.set_hot_wall(wall)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cav.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["plain"] = e0.elapsed_time(e1)
+    cav.close()
+    # the gradient: first on a new handle (allocating the checkpoints and the
+    # backward's buffers), then again from the same initial state on that
+    # handle (buffers kept: the cost of each gradient of a loop)
+    cav = Cavity(n, n, n, stream=stream.cuda_stream, **case)
+    cav.set_hot_wall(wall)
+    f0, g0, s0 = cav.get_state()
+    dth, par = gradient(cav, "_first")
+    res["dL_dRa"] = par["Ra"]
+    res["grad_norm_wall"] = float(np.linalg.norm(dth))
+    res["dL_dv1"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 7))
+    res["dL_dv2"] = float(dth.ravel() @ inputs.gaussian_field(n * n, 1.0, 8))
+    cav.set_state(f0, g0, s0)
+    dth2, par2 = gradient(cav, "")
+    res["repeat_rel_diff"] = float(abs(par2["Ra"] / par["Ra"] - 1.0))
+    cav.close()
     out = {"cube": n, "steps": steps, "forward_ms": res["plain"], "recorded_forward_ms": res["tape"],
            "backward_ms": res["backward"], "adjoint_forward_ratio": res["backward"] / res["plain"],
            "total_over_forward": (res["tape"] + res["backward"]) / res["plain"],
+           "first_gradient": {"recorded_forward_ms": res["tape_first"], "backward_ms": res["backward_first"],
+                              "total_over_forward": (res["tape_first"] + res["backward_first"]) / res["plain"],
+                              "note": "a new handle: includes allocating the checkpoints and the backward's buffers"},
+           "repeat": "timed: a second gradient from the same initial state on the same handle (buffers kept); "
+                     "its dL/dRa differs from the first by %.1e (the state round trip through get/set_state "
+                     "rounds the shifted populations once)" % res["repeat_rel_diff"],
            "dL_dRa": res["dL_dRa"], "grad_norm_wall": res["grad_norm_wall"],
            "dL_dv1": res["dL_dv1"], "dL_dv2": res["dL_dv2"],
            "loss": "final liquid fraction", "checkpoints": "every ceil(sqrt(steps)) steps",

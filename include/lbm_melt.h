@@ -302,7 +302,8 @@ void lbm_melt_destroy(lbm_melt *h);
 
    lbm_melt_tape_forward advances the handle by `steps` steps (as
    lbm_melt_step) and keeps a checkpoint of the state every ckpt_every steps
-   (<= 0: ceil(sqrt(steps))).  The heated-wall field must be set before (no
+   (<= 0: ceil(sqrt(steps)) rounded up to a multiple of the step-graph length
+   when steps are replayed from graphs).  The heated-wall field must be set before (no
    change pending) and stays fixed during the recorded run.
 
    lbm_melt_tape_backward takes seed_dL_dS = dL/dS of the final front (one
@@ -323,7 +324,11 @@ void lbm_melt_destroy(lbm_melt *h);
 lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every);
 lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed_dL_dS, double *dL_dTh, double *dL_dparams,
                                   int ptr_kind);
-/* Release the recorded run. */
+/* Release the recorded run and the adjoint's device buffers.  The
+   checkpoints of a recorded run and the work buffers of the backward are
+   kept with the handle from one gradient to the next (a loop of gradients
+   of one run length allocates once); this call, or lbm_melt_destroy, gives
+   them back. */
 lbm_status lbm_melt_tape_clear(lbm_melt *h);
 
 /* ------------------------------------------------------------------ ensemble

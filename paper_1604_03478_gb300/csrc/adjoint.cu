@@ -367,8 +367,14 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     in.ck = in.cL = -1;
     in.k = -1;
     in.c1 = in.c0 = -1;
-    // ---- loads
+    // ---- loads (everything this column reads, issued before the first
+    // store: the compiler cannot move a load of lam or of a per-column sum
+    // above a store through another pointer, and each such wait is a
+    // memory round trip of a latency-bound kernel)
     const double lams_in = lams[col];
+    const double lsal0 = GHOST ? lsal[col] : 0.0, lgb0 = GHOST ? lgb[col] : 0.0;
+    const double lcoef0 = FRONT ? lcoef[col] : 0.0, lthw0 = lthw[col];
+    float lamf[19];
     if (GHOST) {
         in.slope = slope_terms(p, wp, wq, col);
         in.jn = js[col];
@@ -390,6 +396,8 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                 for (int i = 0; i < 7; ++i) in.gL[i] = snap[(19 + i) * N + in.cL];
 #pragma unroll
                 for (int i = 0; i < 19; ++i) in.fL[i] = snap[i * N + in.cL];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) lamf[i] = lam[i * N + in.cL];
             }
         }
     }
@@ -460,7 +468,7 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                 const float d1 = __fsub_rn(gL[1] - gL[2], __fmul_rn(ux, TL));
                 const float d2 = __fsub_rn(gL[3] - gL[4], __fmul_rn(uy, TL));
                 const float d3 = __fsub_rn(gL[5] - gL[6], __fmul_rn(uz, TL));
-                lsal[col] += -(double)__fmul_rn(
+                lsal[col] = lsal0 + -(double)__fmul_rn(
                     i1, __fadd_rn(__fadd_rn(__fmul_rn(Nl1, d1), __fmul_rn(Nl2, d2)), __fmul_rn(Nl3, d3)));
                 const float ra = 1.0f - p.s_alpha, r4 = 1.0f - p.s_g4, r5 = 1.0f - p.s_g5;
                 float mu[7];
@@ -476,7 +484,7 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
                     __fsub_rn(-__fadd_rn(__fadd_rn(__fmul_rn(mu[1], ux), __fmul_rn(mu[2], uy)), __fmul_rn(mu[3], uz)),
                               __fmul_rn(0.75f, mu[4])),
                     __fmul_rn(__fmul_rn(0.5f, p.gbeta), luz));
-                lgb[col] = __dadd_rn(lgb[col], __dmul_rn(0.5 * (double)(Th - p.dTms), (double)luz));
+                lgb[col] = __dadd_rn(lgb0, __dmul_rn(0.5 * (double)(Th - p.dTms), (double)luz));
                 float og[7];
 #pragma unroll
                 for (int i = 0; i < 7; ++i) og[i] = lTh;
@@ -531,7 +539,7 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
             lams_prev[col] = __dsub_rn(Ls, __dmul_rn(Ls, (double)__fmul_rn(af, dGds)));
             wp_prev[col] = Ls * (double)__fmul_rn(vG, sp);
             wq_prev[col] = Ls * (double)__fmul_rn(vG, sq);
-            lcoef[col] = __dadd_rn(lcoef[col], __dmul_rn(Ls, (double)__fmul_rn(fac, -G)));
+            lcoef[col] = __dadd_rn(lcoef0, __dmul_rn(Ls, (double)__fmul_rn(fac, -G)));
             if (k >= 0) {
                 const float lT1 = -__fmul_rn(La, dGdy1);
 #pragma unroll
@@ -567,9 +575,9 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     }
     if (GHOST && in.cL >= 0) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) lam[i * N + in.cL] += fadd[i];
+        for (int i = 0; i < 19; ++i) lam[i * N + in.cL] = lamf[i] + fadd[i];
     }
-    if (dthw != 0.0) lthw[col] += dthw;
+    if (dthw != 0.0) lthw[col] = lthw0 + dthw;
 }
 
 // Front adjoint of the step t -> t+1 alone (top of a segment): snap and lam
@@ -645,12 +653,66 @@ struct lbm_tape {
     long long T, C, nseg;
     long long thw_gen;               // the handle's wall-field generation when recorded
     size_t ck_bytes;
-    std::vector<void *> ck;          // device checkpoints, one per segment
+    std::vector<void *> ck;          // device checkpoints, one per segment (in the workspace's pool)
     std::vector<int> ck_cur, ck_inflight;
     std::vector<long long> ck_steps;
 };
 
+// The adjoint's device buffers, kept with the handle from one gradient to
+// the next (a loop of gradients of one run length allocates once): the
+// checkpoint pool of the recorded run and the work buffers of the backward,
+// by slot.  A slot is reallocated when a request's size differs; released by
+// lbm_melt_tape_clear and lbm_melt_destroy.
+struct AdjWorkspace {
+    static const int kSlots = 32;
+    void *p[kSlots] = {};
+    size_t b[kSlots] = {};
+};
+
 namespace {
+
+AdjWorkspace *workspace(lbm_melt *h) {
+    if (!h->adj_ws) h->adj_ws = new (std::nothrow) AdjWorkspace();
+    return (AdjWorkspace *)h->adj_ws;
+}
+
+// Device buffer of `bytes` in workspace slot k (the cached one when it has
+// that size).
+cudaError_t ws_alloc(lbm_melt *h, int k, size_t bytes, void **out) {
+    AdjWorkspace *w = workspace(h);
+    if (!w) return cudaErrorMemoryAllocation;
+    if (w->p[k] && w->b[k] == bytes) {
+        *out = w->p[k];
+        return cudaSuccess;
+    }
+    if (w->p[k]) {
+        cudaFree(w->p[k]);
+        w->p[k] = nullptr;
+        w->b[k] = 0;
+    }
+    const cudaError_t e = cudaMalloc(&w->p[k], bytes);
+    if (e != cudaSuccess) {
+        w->p[k] = nullptr;
+        *out = nullptr;
+        return e;
+    }
+    w->b[k] = bytes;
+    *out = w->p[k];
+    return cudaSuccess;
+}
+
+void free_workspace(lbm_melt *h) {
+    AdjWorkspace *w = (AdjWorkspace *)h->adj_ws;
+    if (!w) return;
+    cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < AdjWorkspace::kSlots; ++k)
+        if (w->p[k]) cudaFree(w->p[k]);
+    delete w;
+    h->adj_ws = nullptr;
+}
+
+// Workspace slots: 0 the checkpoint pool, 1.. the backward's buffers.
+const int kSlotCheckpoints = 0, kSlotBackward = 1;
 
 lbm_status tape_err(lbm_melt *h, lbm_status st, const char *fmt, ...) {
     va_list ap;
@@ -701,14 +763,16 @@ void free_tape(lbm_melt *h) {
     lbm_tape *t = (lbm_tape *)h->tape;
     if (!t) return;
     cudaStreamSynchronize(h->stream);
-    for (void *p : t->ck) cudaFree(p);
     delete t;
     h->tape = nullptr;
 }
 
 }  // namespace
 
-void lbm_tape_free(lbm_melt *h) { free_tape(h); }
+void lbm_tape_free(lbm_melt *h) {
+    free_tape(h);
+    free_workspace(h);
+}
 
 LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long ckpt_every) {
     if (!h) return LBM_EINVAL;
@@ -718,7 +782,13 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
                                        "(no heat conduction in the solid)");
     if (h->thw_pending)
         return tape_err(h, LBM_EINVAL, "set the heated-wall field before recording (no change may be pending)");
-    if (ckpt_every <= 0) ckpt_every = (long long)std::ceil(std::sqrt((double)steps));
+    if (ckpt_every <= 0) {
+        // about sqrt(steps), rounded up to whole step graphs (lbm_melt_step
+        // replays graph_steps steps at a time; a remainder runs step by step)
+        ckpt_every = (long long)std::ceil(std::sqrt((double)steps));
+        const long long G = h->graph_steps;
+        if (G > 1 && ckpt_every < steps) ckpt_every = std::min(steps, (ckpt_every + G - 1) / G * G);
+    }
     free_tape(h);
     lbm_tape *t = new (std::nothrow) lbm_tape();
     if (!t) return LBM_ENOMEM;
@@ -728,13 +798,16 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
     t->thw_gen = h->thw_gen;
     t->nseg = (steps + ckpt_every - 1) / ckpt_every;
     t->ck_bytes = state_layout(h, nullptr, nullptr, nullptr);
-    for (long long sgm = 0; sgm < t->nseg; ++sgm) {
-        void *buf = nullptr;
-        cudaError_t e = cudaMalloc(&buf, t->ck_bytes);
+    void *pool = nullptr;
+    {
+        const cudaError_t e = ws_alloc(h, kSlotCheckpoints, (size_t)t->nseg * t->ck_bytes, &pool);
         if (e != cudaSuccess) {
             free_tape(h);
-            return tape_err(h, LBM_ENOMEM, "checkpoint %lld of %lld: %s", sgm, t->nseg, cudaGetErrorString(e));
+            return tape_err(h, LBM_ENOMEM, "%lld checkpoints: %s", t->nseg, cudaGetErrorString(e));
         }
+    }
+    for (long long sgm = 0; sgm < t->nseg; ++sgm) {
+        void *buf = (unsigned char *)pool + (size_t)sgm * t->ck_bytes;
         t->ck.push_back(buf);
         t->ck_cur.push_back(h->cur);
         t->ck_inflight.push_back(h->inflight);
@@ -751,6 +824,7 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
 LBM_API lbm_status lbm_melt_tape_clear(lbm_melt *h) {
     if (!h) return LBM_EINVAL;
     free_tape(h);
+    free_workspace(h);
     return LBM_OK;
 }
 
@@ -805,29 +879,36 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         {(void **)&lthw, nc * 8}, {(void **)&part, nblk * 3 * 8}, {(void **)&lsal, nc * 8},
         {(void **)&lgb, nc * 8}, {(void **)&lcoef, nc * 8}, {(void **)&acc, 4 * 8}};
     lbm_status st = LBM_OK;
-    auto cleanup = [&]() {
-        for (auto &a : al) cudaFree(*a.p);
-        cudaFree(snapb[1]);
-        cudaFree(snap_sb[1]);
-        cudaFree(snap_jsb[1]);
-        cudaFree(snap_nbb[1]);
-    };
-    for (auto &a : al) {
-        cudaError_t e = cudaMalloc(a.p, a.b);
+    // the buffers stay in the handle's workspace for the next gradient; on
+    // an error they are released
+    auto cleanup = [&]() {};
+    const int nal = (int)(sizeof al / sizeof al[0]);
+    for (int k = 0; k < nal; ++k) {
+        cudaError_t e = ws_alloc(h, kSlotBackward + k, al[k].b, al[k].p);
         if (e != cudaSuccess) {
-            cleanup();
+            free_workspace(h);
             return tape_err(h, LBM_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
         }
     }
     // the second snapshot set if the device has room for it (else the
     // segments run one after another through the first)
     int nsets = 2;
-    if (cudaMalloc(&snapb[1], (size_t)(C + 1) * 26 * N * 4) != cudaSuccess ||
-        cudaMalloc(&snap_sb[1], (size_t)(C + 1) * nc * 8) != cudaSuccess ||
-        cudaMalloc(&snap_jsb[1], (size_t)(C + 1) * nc * 4) != cudaSuccess ||
-        cudaMalloc(&snap_nbb[1], (size_t)(C + 1) * nc * 4) != cudaSuccess) {
-        (void)cudaGetLastError();
-        nsets = 1;
+    {
+        const int k2 = kSlotBackward + nal;
+        if (ws_alloc(h, k2, (size_t)(C + 1) * 26 * N * 4, (void **)&snapb[1]) != cudaSuccess ||
+            ws_alloc(h, k2 + 1, (size_t)(C + 1) * nc * 8, (void **)&snap_sb[1]) != cudaSuccess ||
+            ws_alloc(h, k2 + 2, (size_t)(C + 1) * nc * 4, (void **)&snap_jsb[1]) != cudaSuccess ||
+            ws_alloc(h, k2 + 3, (size_t)(C + 1) * nc * 4, (void **)&snap_nbb[1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            AdjWorkspace *w = workspace(h);
+            for (int k = k2; k < k2 + 4; ++k)
+                if (w->p[k]) { cudaFree(w->p[k]); w->p[k] = nullptr; w->b[k] = 0; }
+            snapb[1] = nullptr;
+            snap_sb[1] = nullptr;
+            snap_jsb[1] = nullptr;
+            snap_nbb[1] = nullptr;
+            nsets = 1;
+        }
     }
 #define BCK(call, where)                                                             \
     do {                                                                             \

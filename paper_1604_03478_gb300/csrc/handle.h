@@ -76,6 +76,7 @@ struct lbm_melt {
     float *spost;
     int member;        // owned by an ensemble (whose kernel holds the solid at Tm)
     void *tape;        // recorded run for the adjoint (adjoint.cu)
+    void *adj_ws;      // the adjoint's device buffers, kept between gradients (adjoint.cu)
     // Steps replayed from CUDA graphs (lbm_melt_step): graph_steps steps per
     // replay (0: every step launched on its own).  One instantiated graph per
     // starting (cur, inflight) phase; each records the stream-collide grid
@@ -94,7 +95,8 @@ struct lbm_melt {
     char err[512];
 };
 
-// Release a handle's recorded run (defined with the adjoint).
+// Release a handle's recorded run and the adjoint's buffers (defined with
+// the adjoint).
 void lbm_tape_free(lbm_melt *h);
 // Enqueue one step (stream-collide, front, flip) from phase (cur, inflight)
 // on stream st, the stream-collide grid cut at `height`; advances cur and
