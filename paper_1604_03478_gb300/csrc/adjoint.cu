@@ -375,6 +375,7 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
     const double lsal0 = GHOST ? lsal[col] : 0.0, lgb0 = GHOST ? lgb[col] : 0.0;
     const double lcoef0 = FRONT ? lcoef[col] : 0.0, lthw0 = lthw[col];
     float lamf[19];
+    // stage 1: what depends on the column only
     if (GHOST) {
         in.slope = slope_terms(p, wp, wq, col);
         in.jn = js[col];
@@ -385,42 +386,66 @@ __device__ __forceinline__ void adj_column(const KP &p, int col, const float *__
             in.lgp[i] = lgpost[(long long)i * p.ncols + col];
             in.lTG = __fmaf_rn(w7(i), in.lgp[i], in.lTG);
         }
-        if (in.jn < H) {
-            in.kg = guarded_node(in.sn, H);
-            if (in.kg >= 0) in.Tk = snap_T<FACE>(p, snap, col, in.kg, in.ck);
-            if (in.jn >= 1) {
-                int x, y, z;
-                column_node<FACE>(p, col, in.jn - 1, x, y, z);
-                in.cL = node_index(p, x, y, z);
-#pragma unroll
-                for (int i = 0; i < 7; ++i) in.gL[i] = snap[(19 + i) * N + in.cL];
-#pragma unroll
-                for (int i = 0; i < 19; ++i) in.fL[i] = snap[i * N + in.cL];
-#pragma unroll
-                for (int i = 0; i < 19; ++i) lamf[i] = lam[i * N + in.cL];
-            }
-        }
     }
     if (FRONT) {
         in.sc = s_prev[col];
         in.sp = 0.5f * (float)(s_prev[q * P1 + (pp + 1 < P1 ? pp + 1 : pp)] - s_prev[q * P1 + (pp > 0 ? pp - 1 : pp)]);
         in.sq = 0.5f * (float)(s_prev[(q + 1 < P2 ? q + 1 : q) * P1 + pp] - s_prev[(q > 0 ? q - 1 : q) * P1 + pp]);
-        in.k = guarded_node(in.sc, H);
-        in.y0 = Tw;
-        if (in.k >= 0) {
-            in.y1 = snap_T<FACE>(p, snap, col, in.k, in.c1);
-            if (in.k >= 1) in.y0 = snap_T<FACE>(p, snap, col, in.k - 1, in.c0);
-        }
     }
-    // the g adjoint of up to four nodes: ghost source, guarded node, stencil
-    long long nd[4] = {in.cL, in.ck, in.c1, in.c0};
+    // stage 2: the nodes the column touches (ghost source, guarded node, two
+    // stencil nodes), all loads issued unconditionally from indices clamped
+    // into the column (a node that is not needed is read and ignored), so
+    // that no load waits behind a branch
+    const bool g_on = GHOST && in.jn < H;
+    if (g_on) in.kg = guarded_node(in.sn, H);
+    if (FRONT) in.k = guarded_node(in.sc, H);
+    const bool hasL = g_on && in.jn >= 1, hasK = g_on && in.kg >= 0;
+    const bool has1 = FRONT && in.k >= 0, has0 = FRONT && in.k >= 1;
+    auto node_of = [&](int j) {
+        int x, y, z;
+        column_node<FACE>(p, col, j < 0 ? 0 : j, x, y, z);
+        return node_index(p, x, y, z);
+    };
+    const long long eL = node_of(in.jn - 1), eK = node_of(in.kg), e1 = node_of(in.k), e0 = node_of(in.k - 1);
+    float gK[7], g1[7], g0[7];
+    if (GHOST) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) in.gL[i] = snap[(19 + i) * N + eL];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) in.fL[i] = snap[i * N + eL];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) lamf[i] = lam[i * N + eL];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gK[i] = snap[(19 + i) * N + eK];
+    }
+    if (FRONT) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) g1[i] = snap[(19 + i) * N + e1];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) g0[i] = snap[(19 + i) * N + e0];
+    }
+    // the g adjoint of the four nodes (clamped as above)
+    const long long eff[4] = {eL, eK, e1, e0};
     float base[4][7];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-        if (nd[e] >= 0) {
+        if (e < 2 ? GHOST : FRONT) {
 #pragma unroll
-            for (int i = 0; i < 7; ++i) base[e][i] = lam[(19 + i) * N + nd[e]];
+            for (int i = 0; i < 7; ++i) base[e][i] = lam[(19 + i) * N + eff[e]];
         }
+    // temperatures summed in the order of the forward's front update
+    auto tsum = [&](const float (&g)[7]) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) t += g[i];
+        return p.Ts + t;
+    };
+    if (hasL) in.cL = eL;
+    if (hasK) { in.ck = eK; in.Tk = tsum(gK); }
+    in.y0 = Tw;
+    if (has1) { in.c1 = e1; in.y1 = tsum(g1); }
+    if (has0) { in.c0 = e0; in.y0 = tsum(g0); }
+    long long nd[4] = {in.cL, in.ck, in.c1, in.c0};
     float add[4][7];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
