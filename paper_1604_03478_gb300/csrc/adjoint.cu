@@ -670,6 +670,55 @@ __global__ void __launch_bounds__(256) k_sum_into(const double *__restrict__ v, 
     if (threadIdx.x == 0) *out += sh[0];
 }
 
+// Checkpoint copy of a state whose deep solid nodes are skipped (Tc = Tm):
+// only the heights below the running maximum liquid count + 3 are copied
+// (every node that is not deep, and so every slot the method reads, lies
+// there; the slots above are never read until they have been written again
+// by the steps that follow), with the small per-column arrays.  dir = 0
+// saves (the bound from *jmax, recorded at `bound` in the checkpoint), dir =
+// 1 restores with the recorded bound.  F and G live at offsets offF, offG of
+// the checkpoint, the small arrays at off[k] (byte sizes sz[k]).
+struct CkptSmall {
+    unsigned char *dev[7];
+    size_t off[7], sz[7];
+};
+template <typename ST, int FACE>
+__global__ void __launch_bounds__(256) k_ckpt_move(const __grid_constant__ KP p, ST *__restrict__ F,
+                                                   ST *__restrict__ G, unsigned char *__restrict__ buf,
+                                                   size_t offF, size_t offG, const __grid_constant__ CkptSmall sm,
+                                                   const int *__restrict__ jmax, int *__restrict__ bound, int dir) {
+    int b;
+    if (dir == 0) {
+        b = *jmax + 3;
+        b = b > p.H ? p.H : (b < 1 ? 1 : b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *bound = b;
+    } else {
+        b = *bound;
+    }
+    ST *cF = (ST *)(buf + offF), *cG = (ST *)(buf + offG);
+    const long long plane = FACE == 0 ? (long long)b * p.nx : (long long)b * p.nx * p.ny;  // per z-plane (face 0) or prefix
+    const long long per_dir = FACE == 0 ? plane * p.nz : plane;
+    const long long total = 26 * per_dir;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int i = (int)(e / per_dir);
+        const long long r = e - (long long)i * per_dir;
+        const long long node = FACE == 0 ? (r / plane) * (long long)p.ny * p.nx + r % plane : r;
+        ST *st = i < 19 ? F + (long long)i * p.ld + node : G + (long long)(i - 19) * p.ld + node;
+        ST *ck = i < 19 ? cF + (long long)i * p.ld + node : cG + (long long)(i - 19) * p.ld + node;
+        if (dir == 0) *ck = *st;
+        else *st = *ck;
+    }
+    for (int k = 0; k < 7; ++k) {
+        unsigned int *a = (unsigned int *)sm.dev[k], *c = (unsigned int *)(buf + sm.off[k]);
+        const long long n = (long long)(sm.sz[k] / 4);
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+            if (dir == 0) c[e] = a[e];
+            else a[e] = c[e];
+        }
+    }
+}
+
 }  // namespace lbm
 
 // ------------------------------------------------------------------ tape
@@ -677,7 +726,7 @@ __global__ void __launch_bounds__(256) k_sum_into(const double *__restrict__ v, 
 struct lbm_tape {
     long long T, C, nseg;
     long long thw_gen;               // the handle's wall-field generation when recorded
-    size_t ck_bytes;
+    size_t ck_bytes, ck_bound_off;
     std::vector<void *> ck;          // device checkpoints, one per segment (in the workspace's pool)
     std::vector<int> ck_cur, ck_inflight;
     std::vector<long long> ck_steps;
@@ -784,6 +833,40 @@ lbm_status move_state(lbm_melt *h, unsigned char *buf, int dir) {
     return LBM_OK;
 }
 
+// Save (dir = 0) or restore (dir = 1) a checkpoint: with the deep solid
+// skipped (Tc = Tm), one kernel copying the heights below the running
+// maximum liquid count + 3 (k_ckpt_move; the bound is recorded at byte
+// `boff` of the checkpoint); else the whole state.
+lbm_status move_checkpoint(lbm_melt *h, unsigned char *buf, size_t boff, int dir) {
+    if (!h->kp.skip_deep) return move_state(h, buf, dir);
+    void *dev[9];
+    size_t sz[9], off[9];
+    state_layout(h, dev, sz, off);
+    lbm::CkptSmall sm;
+    for (int k = 0; k < 7; ++k) {
+        sm.dev[k] = (unsigned char *)dev[2 + k];
+        sm.off[k] = off[2 + k];
+        sm.sz[k] = sz[2 + k];
+    }
+    const int blocks = 4 * h->sms;
+    int *bound = (int *)(buf + boff);
+    if (h->precision == 1) {
+        __half *F = (__half *)h->F, *G = (__half *)h->G;
+        if (h->face == 0)
+            lbm::k_ckpt_move<__half, 0><<<blocks, 256, 0, h->stream>>>(h->kp, F, G, buf, off[0], off[1], sm, h->jmax_dev, bound, dir);
+        else
+            lbm::k_ckpt_move<__half, 1><<<blocks, 256, 0, h->stream>>>(h->kp, F, G, buf, off[0], off[1], sm, h->jmax_dev, bound, dir);
+    } else {
+        float *F = (float *)h->F, *G = (float *)h->G;
+        if (h->face == 0)
+            lbm::k_ckpt_move<float, 0><<<blocks, 256, 0, h->stream>>>(h->kp, F, G, buf, off[0], off[1], sm, h->jmax_dev, bound, dir);
+        else
+            lbm::k_ckpt_move<float, 1><<<blocks, 256, 0, h->stream>>>(h->kp, F, G, buf, off[0], off[1], sm, h->jmax_dev, bound, dir);
+    }
+    TCK(cudaGetLastError(), "checkpoint copy");
+    return LBM_OK;
+}
+
 void free_tape(lbm_melt *h) {
     lbm_tape *t = (lbm_tape *)h->tape;
     if (!t) return;
@@ -822,7 +905,8 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
     t->C = ckpt_every;
     t->thw_gen = h->thw_gen;
     t->nseg = (steps + ckpt_every - 1) / ckpt_every;
-    t->ck_bytes = state_layout(h, nullptr, nullptr, nullptr);
+    t->ck_bound_off = state_layout(h, nullptr, nullptr, nullptr);
+    t->ck_bytes = t->ck_bound_off + 256;  // + the recorded height bound
     void *pool = nullptr;
     {
         const cudaError_t e = ws_alloc(h, kSlotCheckpoints, (size_t)t->nseg * t->ck_bytes, &pool);
@@ -837,7 +921,7 @@ LBM_API lbm_status lbm_melt_tape_forward(lbm_melt *h, long long steps, long long
         t->ck_cur.push_back(h->cur);
         t->ck_inflight.push_back(h->inflight);
         t->ck_steps.push_back(h->steps);
-        lbm_status st = move_state(h, (unsigned char *)buf, 0);
+        lbm_status st = move_checkpoint(h, (unsigned char *)buf, t->ck_bound_off, 0);
         if (st != LBM_OK) return st;
         const long long n = std::min(ckpt_every, steps - sgm * ckpt_every);
         st = lbm_melt_step(h, n);
@@ -1090,7 +1174,8 @@ LBM_API lbm_status lbm_melt_tape_backward(lbm_melt *h, const double *seed, doubl
         // stream A: the set's previous reader done, restore the checkpoint,
         // recompute into the set
         if (used[b]) e = cudaStreamWaitEvent(h->stream, ev_rev[b], 0);
-        if (e == cudaSuccess && (st = move_state(h, (unsigned char *)t->ck[sgm], 1)) != LBM_OK) break;
+        if (e == cudaSuccess && (st = move_checkpoint(h, (unsigned char *)t->ck[sgm], t->ck_bound_off, 1)) != LBM_OK)
+            break;
         const int cur0 = t->ck_cur[sgm], infl0 = t->ck_inflight[sgm];
         h->steps = t->ck_steps[sgm];
         if (e == cudaSuccess) {
