@@ -39,6 +39,7 @@ struct lbm_melt {
     double *nu_dev;    // per-column Nusselt numbers (ncols)
     int *status_dev;
     double *sum_dev;
+    unsigned int *ticket;  // last-block ticket of the one-launch column sum (k_sum_once)
     double *red_part;  // scratch: per-block partials of the FP64 totals
     int nred;          // number of partial blocks
     double *totals_dev;  // 7 doubles

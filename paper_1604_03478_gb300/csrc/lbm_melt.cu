@@ -248,6 +248,7 @@ void free_all(lbm_melt *h) {
     cudaFree(h->thw_prev);
     cudaFree(h->status_dev);
     cudaFree(h->sum_dev);
+    cudaFree(h->ticket);
     cudaFree(h->red_part);
     cudaFree(h->totals_dev);
     cudaFree(h->nu_dev);
@@ -316,24 +317,15 @@ lbm_status jmax_readback(lbm_melt *h, bool force = false) {
     return LBM_OK;
 }
 
-// Deterministic FP64 sum of n values in one block (fixed order).
-__global__ void k_sum(const double *__restrict__ v, long long n, double scale, double *__restrict__ out) {
-    __shared__ double sh[1024];
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sh[0] * scale;
-}
-
-// First pass of a two-pass FP64 sum: block b adds the b-th contiguous chunk
-// of v in a fixed order (deterministic for a given n and block count).
-__global__ void k_sum_part(const double *__restrict__ v, long long n, long long chunk, double *__restrict__ part) {
+// scale * (sum of the n values v) in one launch, deterministic for a given
+// n and block count: block b adds the b-th contiguous chunk in a fixed order
+// in strides of the block size, then a tree; the block that finishes last
+// (atomic ticket) adds the partials in block order, writes the result and
+// resets the ticket.
+__global__ void k_sum_once(const double *__restrict__ v, long long n, long long chunk, double scale,
+                           double *part, unsigned int *ticket, double *__restrict__ out) {
     __shared__ double sh[256];
+    __shared__ bool last;
     const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
     double acc = 0.0;
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += v[i];
@@ -343,7 +335,26 @@ __global__ void k_sum_part(const double *__restrict__ v, long long n, long long 
         if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sh[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(part + b);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out = sh[0] * scale;
+        *ticket = 0u;
+    }
 }
 
 __global__ void k_fill_f(float *p, long long n, float v) {
@@ -482,6 +493,7 @@ cudaError_t initial_state(lbm_melt *h) {
     if (e == cudaSuccess && h->spost) e = cudaMemsetAsync(h->spost, 0, 7 * nc * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->jmax_dev, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) {
         k_fill_d<<<nb, 256, 0, h->stream>>>(h->s[0], (long long)nc, d.s0);
         k_fill_f<<<nb, 256, 0, h->stream>>>(h->thw_cur, (long long)nc, (float)Th);
@@ -615,7 +627,7 @@ LBM_API lbm_status lbm_melt_create(const lbm_melt_grid *grid, double Ra, double 
         {(void **)&h->nb[0], nc * 4}, {(void **)&h->nb[1], nc * 4},
         {(void **)&h->s[0], nc * 8}, {(void **)&h->s[1], nc * 8}, {(void **)&h->gpost, 7 * nc * 4},
         {(void **)&h->thw_cur, nc * 4}, {(void **)&h->thw_prev, nc * 4}, {(void **)&h->status_dev, 4},
-        {(void **)&h->sum_dev, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 7 * 8},
+        {(void **)&h->sum_dev, 8}, {(void **)&h->ticket, 8}, {(void **)&h->red_part, kRedBlocks * 4 * 8}, {(void **)&h->totals_dev, 7 * 8},
         {(void **)&h->jmax_dev, sizeof(int)}, {(void **)&h->nu_dev, nc * 8}};
     h->nred = kRedBlocks;
     for (auto &a : allocs) {
@@ -749,14 +761,13 @@ LBM_API lbm_status lbm_melt_get_report(lbm_melt *h, double *rows, long long max_
 }
 
 // scale * (sum of the ncols column values v), into dst on the handle's
-// stream: two passes over the columns (chunks of at least 1024 columns per
+// stream: one launch of k_sum_once (chunks of at least 1024 columns per
 // block, fixed order), then a copy.
 lbm_status enqueue_column_sum(lbm_melt *h, const double *v, double scale, double *dst, int ptr_kind) {
     const long long nc = h->kp.ncols;
     const long long nb = std::max<long long>(1, std::min<long long>(kRedBlocks, (nc + 1023) / 1024));
     const long long chunk = (nc + nb - 1) / nb;
-    k_sum_part<<<(int)nb, 256, 0, h->stream>>>(v, nc, chunk, h->red_part);
-    k_sum<<<1, 1024, 0, h->stream>>>(h->red_part, nb, scale, h->sum_dev);
+    k_sum_once<<<(int)nb, 256, 0, h->stream>>>(v, nc, chunk, scale, h->red_part, h->ticket, h->sum_dev);
     CK(cudaGetLastError(), "sum");
     CK(cudaMemcpyAsync(dst, h->sum_dev, 8, ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
        "copy sum");
