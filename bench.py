@@ -348,7 +348,50 @@ def precision_leg(steps=200, twin_steps=(400, 1000, 2000)):
     out["twin"] = ("64^3 twin of each workload (same parameters, front at 0.4 H), %s steps from the same initial "
                    "state, against the FP64 oracle; FP16 stores g shifted by the mid temperature (Th + Tm) / 2"
                    % ", ".join(str(t) for t in twin_steps))
+    out["full_horizon"] = full_horizon()
     return out
+
+
+def full_horizon(steps=50000):
+    """The precision workload over its configured 50000 steps at 256^3, for
+    both heated faces: FP16 storage against FP32 storage run side by side
+    (the oracle's FP64 run of that length would take hours on the host; FP32
+    stays within 2e-7 of it on the 64^3 twin over the horizons checked), the
+    liquid fraction each reaches, and a control: FP32 against FP32 with the
+    one-node kernels (the same arithmetic rounded differently, differences
+    of 1e-7 per step), which shows how far the convecting flow itself carries
+    rounding differences over that horizon."""
+    import torch
+    from paper_1604_03478_gb300 import Cavity
+    stream = torch.cuda.current_stream()
+    res = {"steps": steps}
+    for face, name in ((0, "side_heated"), (1, "bottom_heated")):
+        cav = {prec: Cavity(N_EDGE, N_EDGE, N_EDGE, precision=prec % 2, stream=stream.cuda_stream,
+                            **dict(CASE, face=face)) for prec in (0, 1, 2)}
+        cav[2].set_node_pairs(0)
+        ms = {}
+        for prec, c in cav.items():
+            e0, e1 = _events()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[prec] = e0.elapsed_time(e1)
+        T32, u32, S32, lf32 = cav[0].get()
+        T16, u16, S16, lf16 = cav[1].get()
+        Tc, uc, Sc, lfc = cav[2].get()
+        for c in cav.values():
+            c.close()
+        res[name] = {"fp32_control_max_abs_dT": float(np.abs(Tc - T32).max()),
+                     "fp32_control_max_abs_dS": float(np.abs(Sc - S32).max()),
+                     "fp32_control_d_liquid_fraction": abs(lfc - lf32),
+                     "fp16_vs_fp32_max_abs_dT": float(np.abs(T16 - T32).max()),
+                     "fp16_vs_fp32_max_abs_du": float(np.abs(u16 - u32).max()),
+                     "fp16_vs_fp32_max_abs_dS": float(np.abs(S16 - S32).max()),
+                     "liquid_fraction_fp32": lf32, "liquid_fraction_fp16": lf16,
+                     "s_fp32": ms[0] * 1e-3, "s_fp16": ms[1] * 1e-3}
+    return res
 
 
 def convection_leg(steps=20000, n=128, every=500, dump_dir=None):
