@@ -253,8 +253,7 @@ lbm_status lbm_melt_set_graph_steps(lbm_melt *h, int steps);
    with an even nx and one otherwise; 0 one node per thread; 1 two nodes per
    thread (x-adjacent nodes as the two lanes of packed FP32x2 arithmetic,
    their populations moved as float2/half2 words where aligned; needs an
-   even nx, else LBM_EINVAL).  With heat conduction in the solid the
-   stream-collide takes one node per thread whatever the mode.  Two nodes
+   even nx, else LBM_EINVAL).  Two nodes
    per thread pay about half the instructions per node and win where the
    grid is large; small grids with a thin liquid layer are latency bound
    and run faster with one. */

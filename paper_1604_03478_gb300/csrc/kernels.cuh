@@ -426,6 +426,21 @@ __device__ __forceinline__ float2 ld_pair(const float *q) { return *(const float
 __device__ __forceinline__ void st_pair(__half *q, float2 v) { __stcs((__half2 *)q, __floats2half2_rn(v.x, v.y)); }
 __device__ __forceinline__ void st_pair(float *q, float2 v) { __stcs((float2 *)q, v); }
 
+// The even step of a pair of liquid nodes (both collide, no phase test).
+template <typename ST, typename IX>
+__device__ __forceinline__ void even_pair_liquid(const KP &p, ST *__restrict__ F, ST *__restrict__ G, IX c) {
+    float2 f[19], g[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = ld_pair(elem<IX>(F, c, i * p.ld));
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g[i] = ld_pair(elem<IX>(G, c, i * p.ld));
+    collide2(p, f, g);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) st_pair(elem<IX>(F, c, opp(i) * p.ld), f[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) st_pair(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
+}
+
 template <typename ST, int FACE, typename IX>
 __device__ __forceinline__ void even_pair(const KP &p, ST *__restrict__ F, ST *__restrict__ G,
                                           const int *__restrict__ js, const int *__restrict__ nb,
@@ -433,17 +448,7 @@ __device__ __forceinline__ void even_pair(const KP &p, ST *__restrict__ F, ST *_
     const int a = axial<FACE>(x, y, z);
     const int col = column<FACE>(p, x, y, z);  // x + 1 is in column col + 1
     if (a < __ldg(js + col) && a < __ldg(js + col + 1)) {
-        const IX c = (IX)node_index(p, x, y, z);
-        float2 f[19], g[7];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) f[i] = ld_pair(elem<IX>(F, c, i * p.ld));
-#pragma unroll
-        for (int i = 0; i < 7; ++i) g[i] = ld_pair(elem<IX>(G, c, i * p.ld));
-        collide2(p, f, g);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) st_pair(elem<IX>(F, c, opp(i) * p.ld), f[i]);
-#pragma unroll
-        for (int i = 0; i < 7; ++i) st_pair(elem<IX>(G, c, opp7(i) * p.ld), g[i]);
+        even_pair_liquid<ST, IX>(p, F, G, (IX)node_index(p, x, y, z));
     } else {
         even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
         even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x + 1, y, z);
@@ -459,27 +464,14 @@ __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_even_pair(const 
     if (k1_pair<FACE>(p, jmax, x, y, z)) even_pair<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
 }
 
-// The odd step for a pair: both nodes on the one-node fast path (liquid, off
-// the walls of the heating axis and of the other in-plane axis, one node
-// below the lowest first-solid node of their 3x3 columns).  Links without
-// an x component move as half2 words; the others node by node, with the x
-// walls (x0 = 0 for lane x, x0 + 1 = nx - 1 for lane y) taken as in odd_node.
+// The odd step of a pair on the fast path (both liquid, off the walls of the
+// heating axis and of the other in-plane axis, every link streaming but
+// those across an x wall).  Links without an x component move as half2 /
+// float2 words; the others node by node, with the x walls (x0 = 0 for lane
+// x, x0 + 1 = nx - 1 for lane y) taken as in odd_node.
 template <typename ST, int FACE, typename IX>
-__device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, ST *__restrict__ F,
-                                         ST *__restrict__ G, const int *__restrict__ js,
-                                         const int *__restrict__ nb, const float *__restrict__ gpost,
-                                         const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
-                                         int y, int z) {
-    const int a = axial<FACE>(x, y, z);
-    const int col = column<FACE>(p, x, y, z);
-    const int q = FACE == 0 ? z : y, nq = FACE == 0 ? p.nz : p.ny;
-    const bool off_qa = q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
-    const bool fast = off_qa && a + 1 < (__ldg(nb + col) >> 16) && a + 1 < (__ldg(nb + col + 1) >> 16);
-    if (!fast) {
-        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
-        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x + 1, y, z);
-        return;
-    }
+__device__ __forceinline__ void odd_pair_liquid(const KP &p, const Links *lk, ST *__restrict__ F,
+                                                ST *__restrict__ G, int x, int y, int z) {
     const IX c = (IX)node_index(p, x, y, z), c1 = c + 1;
     const bool xlo = x == 0, xhi = x + 1 == p.nx - 1;
     float2 f[19], g[7];
@@ -522,6 +514,29 @@ __device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, ST *__res
             Store<ST>::st_stream(elem<IX>(G, c1, tx(i) > 0 && xhi ? opp7(i) * p.ld : lk->gout[i]), g[i].y);
         }
     }
+}
+
+// The odd step for a pair: both nodes on the one-node fast path (liquid, off
+// the walls of the heating axis and of the other in-plane axis, one node
+// below the lowest first-solid node of their 3x3 columns) take
+// odd_pair_liquid, any other pair the one-node code node by node.
+template <typename ST, int FACE, typename IX>
+__device__ __forceinline__ void odd_pair(const KP &p, const Links *lk, ST *__restrict__ F,
+                                         ST *__restrict__ G, const int *__restrict__ js,
+                                         const int *__restrict__ nb, const float *__restrict__ gpost,
+                                         const float *__restrict__ thw_rd, const float *__restrict__ thw_wr, int x,
+                                         int y, int z) {
+    const int a = axial<FACE>(x, y, z);
+    const int col = column<FACE>(p, x, y, z);
+    const int q = FACE == 0 ? z : y, nq = FACE == 0 ? p.nz : p.ny;
+    const bool off_qa = q >= 1 && q <= nq - 2 && a >= 1 && a <= p.H - 2;
+    const bool fast = off_qa && a + 1 < (__ldg(nb + col) >> 16) && a + 1 < (__ldg(nb + col + 1) >> 16);
+    if (!fast) {
+        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
+        odd_node<ST, FACE>(p, lk, F, G, js, nb, gpost, thw_rd, thw_wr, x + 1, y, z);
+        return;
+    }
+    odd_pair_liquid<ST, FACE, IX>(p, lk, F, G, x, y, z);
 }
 
 template <typename ST, int FACE, typename IX>

@@ -174,7 +174,7 @@ lbm_status cuda_err(lbm_melt *h, cudaError_t e, const char *where) {
 // are latency bound and run faster with one node per thread (96^3 adjoint
 // forward 54 against 61 ms, 128^3 convection 33 against 35 us per step).
 bool use_pairs(const lbm_melt *h) {
-    if (h->kp.nx % 2 != 0 || h->kp.cond) return false;
+    if (h->kp.nx % 2 != 0) return false;
     return h->pairs_mode < 0 ? h->d.N > kGraphMaxNodes : h->pairs_mode == 1;
 }
 

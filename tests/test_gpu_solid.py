@@ -28,8 +28,10 @@ def lib():
     return Cavity
 
 
-def _pair(lib, orc, shape, **kw):
-    return lib(*shape, **kw), orc.Oracle(*shape, **kw)
+def _pair(lib, orc, shape, pairs=-1, **kw):
+    gpu = lib(*shape, **kw)
+    gpu.set_node_pairs(pairs)  # -1: the default choice (one node per thread at these sizes); 1: two
+    return gpu, orc.Oracle(*shape, **kw)
 
 
 def _compare(gpu, o, tol_T=TOL_T, tol_lf=TOL_LF, tol_u=1e-4):
@@ -67,26 +69,28 @@ def test_subcooled_conduction_melting(lib, orc, face, shape, kappa):
 
 @pytest.mark.parametrize("face,shape", [(0, (40, 24, 20)), (1, (36, 20, 26))])
 @pytest.mark.parametrize("steps", [150, 151])
-def test_subcooled_convection_melting(lib, orc, face, shape, steps):
+@pytest.mark.parametrize("pairs", [-1, 1])
+def test_subcooled_convection_melting(lib, orc, face, shape, steps, pairs):
     """Ra > 0 with a subcooled solid, both heated faces, both AA phases, a
     ragged x extent."""
     kw = dict(face=face, Ra=1e5, Pr=0.1, Ste=1.0, Ma=0.2, s0=3.0, derive=True, Tc=-0.5, Tm=0.0, solid=1,
               ks_kl=1.5)
-    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu, o = _pair(lib, orc, shape, pairs, **kw)
     gpu.step(steps)
     o.step(steps)
     _compare(gpu, o)
 
 
 @pytest.mark.parametrize("face", [0, 1])
-def test_refreezing_front(lib, orc, face):
+@pytest.mark.parametrize("pairs", [-1, 1])
+def test_refreezing_front(lib, orc, face, pairs):
     """A front started near the cold wall recedes (the solid's conduction
     flux exceeds the liquid's): nodes refreeze every few steps in both AA
     phases."""
-    shape = (9, 32, 7) if face == 0 else (9, 7, 32)
+    shape = (10, 32, 7) if face == 0 else (10, 7, 32)
     kw = dict(face=face, Ra=0.0, Ste=1.0, Th=1.0, Tc=-1.0, Tm=0.0, s0=28.0, s_nu=1.25, s_alpha=1.0, solid=1,
               ks_kl=1.0)
-    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu, o = _pair(lib, orc, shape, pairs, **kw)
     gpu.step(301)
     o.step(301)
     _compare(gpu, o, tol_u=1e-6)
@@ -114,12 +118,13 @@ def _random_state(o, seed, s_lo, s_hi, Tc, amp=2e-3):
 
 @pytest.mark.parametrize("face", [0, 1])
 @pytest.mark.parametrize("nsteps", [1, 2, 3])
-def test_steps_from_random_state(lib, orc, face, nsteps):
+@pytest.mark.parametrize("pairs", [-1, 1])
+def test_steps_from_random_state(lib, orc, face, nsteps, pairs):
     """A non-flat front and perturbed populations in both phases: after 1,
     2, 3 steps every distribution agrees (liquid f; g of every node)."""
-    shape = (13, 10, 9) if face == 0 else (13, 9, 10)
+    shape = (14, 10, 9) if face == 0 else (14, 9, 10)
     kw = dict(face=face, Ra=2e4, Pr=0.5, Ste=0.3, Ma=0.15, derive=True, Tc=-0.6, Tm=0.0, solid=1, ks_kl=1.8)
-    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu, o = _pair(lib, orc, shape, pairs, **kw)
     f, g, s = _random_state(o, 7 + face, 2.2, 7.8, -0.6)
     o.set_state(f.astype(np.float64), g.astype(np.float64), s)
     gpu.set_state(f, g, s)
@@ -135,14 +140,15 @@ def test_steps_from_random_state(lib, orc, face, nsteps):
 
 @pytest.mark.parametrize("face", [0, 1])
 @pytest.mark.parametrize("direction", ["melt", "freeze"])
-def test_flips_after_even_and_odd_steps(lib, orc, face, direction):
+@pytest.mark.parametrize("pairs", [-1, 1])
+def test_flips_after_even_and_odd_steps(lib, orc, face, direction, pairs):
     """Fronts placed just below node centres (melting) or just above them
     under a strongly subcooled solid (refreezing), so that nodes change
     phase in the first (even, values in flight) and second (odd) steps."""
     shape = (12, 10, 11) if face == 0 else (12, 11, 10)
     Tc = -0.2 if direction == "melt" else -4.0
     kw = dict(face=face, Ra=0.0, Ste=1.0, Tc=Tc, Tm=0.0, s_nu=1.3, s_alpha=1.5, solid=1, ks_kl=1.0)
-    gpu, o = _pair(lib, orc, shape, **kw)
+    gpu, o = _pair(lib, orc, shape, pairs, **kw)
     f, g, s = _random_state(o, 21 + face, 2.0, 6.0, Tc)
     if direction == "melt":
         s = np.floor(s) + 0.5 - inputs.uniform(s.shape, 0.01, 0.03, 5)
