@@ -3,8 +3,11 @@
 //
 // One step of the method (Li, Yang & Zhang, arXiv:1604.03478, section 2):
 //   k_even / k_odd : fused stream + collide of f (D3Q19 MRT, Eqs. 1-3) and
-//                    g (D3Q7 MRT, Eqs. 4-5), in place by the AA pattern;
-//   k_front        : interfacial tracking, Eq. 6, one thread per column, FP64;
+//                    g (D3Q7 MRT, Eqs. 4-5), in place by the AA pattern, one
+//                    node per thread (k_even_pair / k_odd_pair: two
+//                    x-adjacent nodes per thread in packed FP32x2 arithmetic);
+//   k_front        : interfacial tracking, Eq. 6, one thread per column (FP64
+//                    fronts, FP32 gradient and speed);
 //   k_flip         : phase flip of the nodes the front crossed.
 //
 // AA pattern.  A step that starts from the natural layout (slot i of node x
