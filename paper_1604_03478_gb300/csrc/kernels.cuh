@@ -32,6 +32,16 @@
 
 namespace lbm {
 
+// Programmatic dependent launch: the kernels of a step are launched so that
+// the next one may be scheduled while the previous one drains; each waits
+// for its predecessor's completion (and memory) before its first access,
+// then lets its own successor be scheduled.  Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void step_launch_wait() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 template <int FACE> __device__ __forceinline__ long long off19(const KP &p, int i) {
     return (long long)ex(i) + (long long)ey(i) * p.nx + (long long)ez(i) * p.nx * p.ny;
 }
@@ -184,6 +194,7 @@ template <typename ST, int FACE, typename IX>
 __global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_even(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                               const int *__restrict__ js, const int *__restrict__ nb,
                                               const float *__restrict__ gpost, const int *jmax) {
+    step_launch_wait();
     int x, y, z;
     if (k1_node<FACE>(p, jmax, x, y, z)) even_node<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
 }
@@ -365,6 +376,7 @@ __global__ void __launch_bounds__(128, k1_min_blocks<ST>()) k_odd(const __grid_c
                                              const float *__restrict__ gpost, const float *__restrict__ thw_rd,
                                              const float *__restrict__ thw_wr, const __grid_constant__ Links lk,
                                              const int *jmax) {
+    step_launch_wait();
     int x, y, z;
     if (k1_node<FACE>(p, jmax, x, y, z)) odd_node<ST, FACE>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
 }
@@ -463,6 +475,7 @@ __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_even_pair(const 
                                                       ST *__restrict__ G, const int *__restrict__ js,
                                                       const int *__restrict__ nb, const float *__restrict__ gpost,
                                                       const int *jmax) {
+    step_launch_wait();
     int x, y, z;
     if (k1_pair<FACE>(p, jmax, x, y, z)) even_pair<ST, FACE, IX>(p, F, G, js, nb, gpost, x, y, z);
 }
@@ -549,6 +562,7 @@ __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_odd_pair(const _
                                                      const float *__restrict__ thw_rd,
                                                      const float *__restrict__ thw_wr,
                                                      const __grid_constant__ Links lk, const int *jmax) {
+    step_launch_wait();
     int x, y, z;
     if (k1_pair<FACE>(p, jmax, x, y, z)) odd_pair<ST, FACE, IX>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z);
 }
@@ -903,6 +917,7 @@ __global__ void __launch_bounds__(128) k_front(const __grid_constant__ KP p, con
                                                float *__restrict__ gpost, const float *__restrict__ thw,
                                                int inflight, int move, int *__restrict__ status,
                                                int *__restrict__ jmax) {
+    step_launch_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     int jn = -1;
     if (col < p.ncols) jn = front_column<ST, FACE>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col);
@@ -999,6 +1014,7 @@ template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_flip(const __grid_constant__ KP p, ST *__restrict__ F, const int *__restrict__ js_old,
                                               const int *__restrict__ js_new, int *__restrict__ nb_new,
                                               int inflight, int do_flip) {
+    step_launch_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= p.ncols) return;
     flip_column<ST, FACE>(p, F, js_old, js_new, nb_new, inflight, do_flip, col);

@@ -7,16 +7,39 @@
 
 namespace lbm {
 
+// The step's kernels (stream-collide, front, flip) are launched with
+// programmatic stream serialization (see step_launch_wait) when LBM_PDL.
+#ifndef LBM_PDL
+#define LBM_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+static void launch_step_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
+#if LBM_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kern, args...);
+#else
+    kern<<<grd, blk, 0, st>>>(args...);
+#endif
+}
+
 template <typename ST, typename IXE>
 static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, dim3 blk, cudaStream_t st) {
     const int *jm = p.skip_deep ? b.jmax : nullptr;
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) k_odd<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even<ST, 0, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) launch_step_kernel(k_odd<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else launch_step_kernel(k_even<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
-        if (odd) k_odd<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even<ST, 1, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) launch_step_kernel(k_odd<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else launch_step_kernel(k_even<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     }
 }
 
@@ -33,11 +56,11 @@ static void launch_sc_pair(const KP &p, int face, int odd, const Bufs &b, dim3 b
     half_x.nx = p.nx / 2;
     dim3 grd = k1_grid(half_x, blk, face, b.k1_height);
     if (face == 0) {
-        if (odd) k_odd_pair<ST, 0, IXO><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even_pair<ST, 0, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) launch_step_kernel(k_odd_pair<ST, 0, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else launch_step_kernel(k_even_pair<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
-        if (odd) k_odd_pair<ST, 1, IXO><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else k_even_pair<ST, 1, IXE><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) launch_step_kernel(k_odd_pair<ST, 1, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else launch_step_kernel(k_even_pair<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     }
 }
 
@@ -65,9 +88,9 @@ cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, con
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
-        k_front<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
+        launch_step_kernel(k_front<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
     else
-        k_front<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
+        launch_step_kernel(k_front<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
     return cudaGetLastError();
 }
 
@@ -75,8 +98,8 @@ template <typename ST>
 cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, int do_flip, const Bufs &b, cudaStream_t st) {
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     ST *F = (ST *)b.F;
-    if (face == 0) k_flip<ST, 0><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
-    else k_flip<ST, 1><<<grd, blk, 0, st>>>(p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
+    if (face == 0) launch_step_kernel(k_flip<ST, 0>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
+    else launch_step_kernel(k_flip<ST, 1>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
     return cudaGetLastError();
 }
 
