@@ -66,6 +66,7 @@ template <typename ST, int FACE, typename IX>
 __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_even_pair_cond(
     const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
     const int *__restrict__ nb, const float *__restrict__ gpost, const float *__restrict__ spost) {
+    step_launch_wait();
     int x, y, z;
     if (k1_pair<FACE>(p, nullptr, x, y, z)) even_pair_cond<ST, FACE, IX>(p, F, G, js, nb, gpost, spost, x, y, z);
 }
@@ -124,9 +125,26 @@ __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_odd_pair_cond(
     const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G, const int *__restrict__ js,
     const int *__restrict__ nb, const float *__restrict__ gpost, const float *__restrict__ thw_rd,
     const float *__restrict__ thw_wr, const __grid_constant__ Links lk, const float *__restrict__ spost) {
+    step_launch_wait();
     int x, y, z;
     if (k1_pair<FACE>(p, nullptr, x, y, z))
         odd_pair_cond<ST, FACE, IX>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, spost, x, y, z);
+}
+
+// The conduction step's kernels are launched like the plain step's, with
+// programmatic stream serialization (see step_launch_wait).
+template <typename... KArgs, typename... Args>
+static void launch_cond_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Two nodes per thread, element indices in IX (32 bits whenever all fit).
@@ -134,11 +152,11 @@ template <typename ST, typename IX>
 static void launch_pair_cond(const KP &p, int face, int odd, const Bufs &b, dim3 g2, dim3 blk, cudaStream_t st) {
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) k_odd_pair_cond<ST, 0, IX><<<g2, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else k_even_pair_cond<ST, 0, IX><<<g2, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) launch_cond_kernel(k_odd_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else launch_cond_kernel(k_even_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     } else {
-        if (odd) k_odd_pair_cond<ST, 1, IX><<<g2, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else k_even_pair_cond<ST, 1, IX><<<g2, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) launch_cond_kernel(k_odd_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else launch_cond_kernel(k_even_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     }
 }
 
@@ -155,11 +173,11 @@ cudaError_t LaunchCond<ST>::stream_collide(const KP &p, int face, int odd, const
     }
     const dim3 grd = k1_grid(p, blk, face, p.H);
     if (face == 0) {
-        if (odd) k_odd_cond<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else k_even_cond<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) launch_cond_kernel(k_odd_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else launch_cond_kernel(k_even_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     } else {
-        if (odd) k_odd_cond<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else k_even_cond<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) launch_cond_kernel(k_odd_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else launch_cond_kernel(k_even_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     }
     return cudaGetLastError();
 }
@@ -169,11 +187,11 @@ cudaError_t LaunchCond<ST>::front(const KP &p, int face, int inflight, int move,
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
-        k_front_cond<ST, 0><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
-                                                 inflight, move, b.status);
+        launch_cond_kernel(k_front_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
+                           inflight, move, b.status);
     else
-        k_front_cond<ST, 1><<<grd, blk, 0, st>>>(p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
-                                                 inflight, move, b.status);
+        launch_cond_kernel(k_front_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
+                           inflight, move, b.status);
     return cudaGetLastError();
 }
 

@@ -204,6 +204,7 @@ template <typename ST, int FACE>
 __global__ void __launch_bounds__(128) k_even_cond(const __grid_constant__ KP p, ST *__restrict__ F, ST *__restrict__ G,
                                                    const int *__restrict__ js, const int *__restrict__ nb,
                                                    const float *__restrict__ gpost, const float *__restrict__ spost) {
+    step_launch_wait();
     int x, y, z;
     if (k1_node<FACE>(p, nullptr, x, y, z)) even_node<ST, FACE, long long, true>(p, F, G, js, nb, gpost, x, y, z, spost);
 }
@@ -388,6 +389,7 @@ __global__ void __launch_bounds__(128) k_odd_cond(const __grid_constant__ KP p, 
                                                   const float *__restrict__ gpost, const float *__restrict__ thw_rd,
                                                   const float *__restrict__ thw_wr, const __grid_constant__ Links lk,
                                                   const float *__restrict__ spost) {
+    step_launch_wait();
     int x, y, z;
     if (k1_node<FACE>(p, nullptr, x, y, z))
         odd_node<ST, FACE, true, true>(p, &lk, F, G, js, nb, gpost, thw_rd, thw_wr, x, y, z, spost);
@@ -934,6 +936,7 @@ __global__ void __launch_bounds__(128) k_front_cond(const __grid_constant__ KP p
                                                     double *__restrict__ s_next, float *__restrict__ gpost,
                                                     float *__restrict__ spost, const float *__restrict__ thw,
                                                     int inflight, int move, int *__restrict__ status) {
+    step_launch_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col < p.ncols)
         front_column<ST, FACE, true, true>(p, F, G, js, js_next, s, s_next, gpost, thw, inflight, move, status, col,
