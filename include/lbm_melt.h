@@ -358,8 +358,8 @@ lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *cuda_str
 lbm_status lbm_ensemble_step(lbm_ensemble *e, long long nsteps);
 
 /* Launch shape: threads per block (64, 128 or 256; a block covers an x-y
-   tile of one cavity), nodes per thread in the stream-collide phase (1, 2 or
-   4 consecutive z-planes) and steps per graph replay (even, >= 2).  The grid
+   tile of one cavity), nodes per thread in the stream-collide phase (1, 2,
+   4 or 8 consecutive z-planes) and steps per graph replay (even, >= 2).  The grid
    is the co-resident maximum for that shape. */
 lbm_status lbm_ensemble_set_launch(lbm_ensemble *e, int block, int nodes_per_thread, int graph_steps);
 

@@ -18,7 +18,7 @@ from . import build as _build
 
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 CAVITY_SHAPES = ((128, 1), (64, 2), (32, 4))
-ENSEMBLE_SHAPES = ((64, 2), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2))
+ENSEMBLE_SHAPES = ((64, 2), (128, 1), (128, 2), (128, 4), (128, 8), (256, 1), (256, 2), (256, 4))
 
 
 def _device_key():

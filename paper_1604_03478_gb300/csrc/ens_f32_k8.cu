@@ -1,0 +1,5 @@
+// ens_f32_k8.cu -- the batched form's persistent kernel for FP32 storage and
+// 8 z-planes per item, in a translation unit of its own (parallel build).
+#include "ensemble_kernel.cuh"
+
+const void *lbm::ens_kernel_f32_k8() { return (const void *)lbm::k_ensemble<float, 8>; }

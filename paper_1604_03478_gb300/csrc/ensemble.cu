@@ -76,11 +76,13 @@ const void *kernel_ptr(int precision, int K) {
     if (precision == 1) {
         if (K == 1) return lbm::ens_kernel_f16_k1();
         if (K == 2) return lbm::ens_kernel_f16_k2();
-        return lbm::ens_kernel_f16_k4();
+        if (K == 4) return lbm::ens_kernel_f16_k4();
+        return lbm::ens_kernel_f16_k8();
     }
     if (K == 1) return lbm::ens_kernel_f32_k1();
     if (K == 2) return lbm::ens_kernel_f32_k2();
-    return lbm::ens_kernel_f32_k4();
+    if (K == 4) return lbm::ens_kernel_f32_k4();
+    return lbm::ens_kernel_f32_k8();
 }
 
 // Tile of a cavity for the block size: a power of two from 32 to 128 wide
@@ -268,8 +270,8 @@ LBM_API lbm_status lbm_ensemble_set_launch(lbm_ensemble *e, int block, int nodes
     if (!e) return LBM_EINVAL;
     if (block != 64 && block != 128 && block != 256)
         return ens_err(e, LBM_EINVAL, "block must be 64, 128 or 256");
-    if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4)
-        return ens_err(e, LBM_EINVAL, "nodes_per_thread must be 1, 2 or 4");
+    if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4 && nodes_per_thread != 8)
+        return ens_err(e, LBM_EINVAL, "nodes_per_thread must be 1, 2, 4 or 8");
     if (graph_steps < 2 || (graph_steps & 1)) return ens_err(e, LBM_EINVAL, "graph_steps must be even and >= 2");
     e->block = block;
     e->K = nodes_per_thread;

@@ -224,7 +224,9 @@ namespace lbm {
 const void *ens_kernel_f32_k1();
 const void *ens_kernel_f32_k2();
 const void *ens_kernel_f32_k4();
+const void *ens_kernel_f32_k8();
 const void *ens_kernel_f16_k1();
 const void *ens_kernel_f16_k2();
 const void *ens_kernel_f16_k4();
+const void *ens_kernel_f16_k8();
 }  // namespace lbm
