@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128, pair_min_blocks<ST>()) k_odd_pair_cond(
 // The conduction step's kernels are launched like the plain step's, with
 // programmatic stream serialization (see step_launch_wait).
 template <typename... KArgs, typename... Args>
-static void launch_cond_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
+static cudaError_t launch_cond_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grd;
     cfg.blockDim = blk;
@@ -144,19 +144,19 @@ static void launch_cond_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaS
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    (void)cudaLaunchKernelEx(&cfg, kern, args...);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Two nodes per thread, element indices in IX (32 bits whenever all fit).
 template <typename ST, typename IX>
-static void launch_pair_cond(const KP &p, int face, int odd, const Bufs &b, dim3 g2, dim3 blk, cudaStream_t st) {
+static cudaError_t launch_pair_cond(const KP &p, int face, int odd, const Bufs &b, dim3 g2, dim3 blk, cudaStream_t st) {
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) launch_cond_kernel(k_odd_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else launch_cond_kernel(k_even_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) return launch_cond_kernel(k_odd_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else return launch_cond_kernel(k_even_pair_cond<ST, 0, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     } else {
-        if (odd) launch_cond_kernel(k_odd_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else launch_cond_kernel(k_even_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) return launch_cond_kernel(k_odd_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else return launch_cond_kernel(k_even_pair_cond<ST, 1, IX>, g2, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     }
 }
 
@@ -167,19 +167,17 @@ cudaError_t LaunchCond<ST>::stream_collide(const KP &p, int face, int odd, const
         KP half_x = p;
         half_x.nx = p.nx / 2;
         const dim3 g2 = k1_grid(half_x, blk, face, p.H);
-        if (19LL * p.ld < (1LL << 32)) launch_pair_cond<ST, unsigned>(p, face, odd, b, g2, blk, st);
-        else launch_pair_cond<ST, long long>(p, face, odd, b, g2, blk, st);
-        return cudaGetLastError();
+        if (19LL * p.ld < (1LL << 32)) return launch_pair_cond<ST, unsigned>(p, face, odd, b, g2, blk, st);
+        return launch_pair_cond<ST, long long>(p, face, odd, b, g2, blk, st);
     }
     const dim3 grd = k1_grid(p, blk, face, p.H);
     if (face == 0) {
-        if (odd) launch_cond_kernel(k_odd_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else launch_cond_kernel(k_even_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) return launch_cond_kernel(k_odd_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else return launch_cond_kernel(k_even_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     } else {
-        if (odd) launch_cond_kernel(k_odd_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
-        else launch_cond_kernel(k_even_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
+        if (odd) return launch_cond_kernel(k_odd_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, b.spost);
+        else return launch_cond_kernel(k_even_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.spost);
     }
-    return cudaGetLastError();
 }
 
 template <typename ST>
@@ -187,12 +185,10 @@ cudaError_t LaunchCond<ST>::front(const KP &p, int face, int inflight, int move,
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
-        launch_cond_kernel(k_front_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
-                           inflight, move, b.status);
-    else
-        launch_cond_kernel(k_front_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost, b.thw_wr,
-                           inflight, move, b.status);
-    return cudaGetLastError();
+        return launch_cond_kernel(k_front_cond<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost,
+                                  b.spost, b.thw_wr, inflight, move, b.status);
+    return launch_cond_kernel(k_front_cond<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.spost,
+                              b.thw_wr, inflight, move, b.status);
 }
 
 template struct LaunchCond<float>;

@@ -13,7 +13,7 @@ namespace lbm {
 #define LBM_PDL 1
 #endif
 template <typename... KArgs, typename... Args>
-static void launch_step_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
+static cudaError_t launch_step_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaStream_t st, Args... args) {
 #if LBM_PDL
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grd;
@@ -24,22 +24,23 @@ static void launch_step_kernel(void (*kern)(KArgs...), dim3 grd, dim3 blk, cudaS
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    (void)cudaLaunchKernelEx(&cfg, kern, args...);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 #else
     kern<<<grd, blk, 0, st>>>(args...);
+    return cudaGetLastError();
 #endif
 }
 
 template <typename ST, typename IXE>
-static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, dim3 blk, cudaStream_t st) {
+static cudaError_t launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, dim3 blk, cudaStream_t st) {
     const int *jm = p.skip_deep ? b.jmax : nullptr;
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     if (face == 0) {
-        if (odd) launch_step_kernel(k_odd<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else launch_step_kernel(k_even<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) return launch_step_kernel(k_odd<ST, 0>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else return launch_step_kernel(k_even<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
-        if (odd) launch_step_kernel(k_odd<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else launch_step_kernel(k_even<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) return launch_step_kernel(k_odd<ST, 1>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else return launch_step_kernel(k_even<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     }
 }
 
@@ -49,18 +50,18 @@ static void launch_sc(const KP &p, int face, int odd, const Bufs &b, dim3 grd, d
 // An even nx: two nodes per thread (k_even_pair / k_odd_pair), the grid's x
 // extent covering nx / 2 threads.
 template <typename ST, typename IXE, typename IXO>
-static void launch_sc_pair(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
+static cudaError_t launch_sc_pair(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
     const int *jm = p.skip_deep ? b.jmax : nullptr;
     ST *F = (ST *)b.F, *G = (ST *)b.G;
     KP half_x = p;
     half_x.nx = p.nx / 2;
     dim3 grd = k1_grid(half_x, blk, face, b.k1_height);
     if (face == 0) {
-        if (odd) launch_step_kernel(k_odd_pair<ST, 0, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else launch_step_kernel(k_even_pair<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) return launch_step_kernel(k_odd_pair<ST, 0, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else return launch_step_kernel(k_even_pair<ST, 0, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     } else {
-        if (odd) launch_step_kernel(k_odd_pair<ST, 1, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
-        else launch_step_kernel(k_even_pair<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
+        if (odd) return launch_step_kernel(k_odd_pair<ST, 1, IXO>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, b.thw_rd, b.thw_wr, *b.lk, jm);
+        else return launch_step_kernel(k_even_pair<ST, 1, IXE>, grd, blk, st, p, F, G, b.js, b.nb, b.gpost, jm);
     }
 }
 
@@ -72,14 +73,12 @@ template <typename ST>
 cudaError_t Launch<ST>::stream_collide(const KP &p, int face, int odd, const Bufs &b, dim3 blk, cudaStream_t st) {
     if (p.cond) return LaunchCond<ST>::stream_collide(p, face, odd, b, blk, st);
     if (b.pairs && p.nx % 2 == 0) {
-        if (19LL * p.ld < (1LL << 32)) launch_sc_pair<ST, unsigned, LBM_PAIR_ODD_IX>(p, face, odd, b, blk, st);
-        else launch_sc_pair<ST, long long, long long>(p, face, odd, b, blk, st);
-        return cudaGetLastError();
+        if (19LL * p.ld < (1LL << 32)) return launch_sc_pair<ST, unsigned, LBM_PAIR_ODD_IX>(p, face, odd, b, blk, st);
+        return launch_sc_pair<ST, long long, long long>(p, face, odd, b, blk, st);
     }
     const dim3 grd = k1_grid(p, blk, face, b.k1_height);
-    if (19LL * p.ld < (1LL << 32)) launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
-    else launch_sc<ST, long long>(p, face, odd, b, grd, blk, st);
-    return cudaGetLastError();
+    if (19LL * p.ld < (1LL << 32)) return launch_sc<ST, unsigned>(p, face, odd, b, grd, blk, st);
+    return launch_sc<ST, long long>(p, face, odd, b, grd, blk, st);
 }
 
 template <typename ST>
@@ -88,19 +87,16 @@ cudaError_t Launch<ST>::front(const KP &p, int face, int inflight, int move, con
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     const ST *F = (const ST *)b.F, *G = (const ST *)b.G;
     if (face == 0)
-        launch_step_kernel(k_front<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
-    else
-        launch_step_kernel(k_front<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
-    return cudaGetLastError();
+        return launch_step_kernel(k_front<ST, 0>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
+    return launch_step_kernel(k_front<ST, 1>, grd, blk, st, p, F, G, b.js, b.js_next, b.s, b.s_next, b.gpost, b.thw_wr, inflight, move, b.status, b.jmax);
 }
 
 template <typename ST>
 cudaError_t Launch<ST>::flip(const KP &p, int face, int inflight, int do_flip, const Bufs &b, cudaStream_t st) {
     const dim3 blk(b.cblk), grd = col_grid(p.ncols, b.cblk);
     ST *F = (ST *)b.F;
-    if (face == 0) launch_step_kernel(k_flip<ST, 0>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
-    else launch_step_kernel(k_flip<ST, 1>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
-    return cudaGetLastError();
+    if (face == 0) return launch_step_kernel(k_flip<ST, 0>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
+    return launch_step_kernel(k_flip<ST, 1>, grd, blk, st, p, F, b.js, b.js_next, b.nb_next, inflight, do_flip);
 }
 
 template <typename ST>
