@@ -14,9 +14,17 @@
 // spills) and whether the node variants are out-of-line functions.  Measured
 // on the 48-cavity workload over 100 steps (before the dynamic tile
 // distribution): 3 blocks 14.5 k MLUPS, 2 blocks (up to 128 registers, no
-// spills) 13.3 k.
+// spills) 13.3 k.  With 8 z-planes per item over 2000 steps: 3 blocks 23.9 k,
+// 4 blocks (64 registers, 308 bytes of spills) 23.1 k, a cap of 72
+// registers (7 blocks of 128) 23.8 k.
 #ifndef LBM_ENS_MINB
 #define LBM_ENS_MINB 3
+#endif
+// LBM_ENS_MAXNREG, when defined, caps the registers directly instead.
+#ifdef LBM_ENS_MAXNREG
+#define ENS_BOUNDS __maxnreg__(LBM_ENS_MAXNREG)
+#else
+#define ENS_BOUNDS __launch_bounds__(256, LBM_ENS_MINB)
 #endif
 #ifndef LBM_ENS_NOINLINE
 #define LBM_ENS_NOINLINE 0
@@ -124,7 +132,10 @@ ENS_FN void ens_odd(const CavDesc &d, int cur, const float *trd, int x, int y, i
 }
 
 // One column of phase 2 (front update; returns the new liquid count) or 3
-// (flip; returns -1).
+// (flip; returns -1).  The front update does not load the ghost's likely
+// source node with the gradient stencil (as k_front does): under this
+// kernel's register cap that spilled 1.3 KB a thread and slowed every phase
+// (19.8 k against 23.2 k MLUPS on the 48-cavity workload).
 template <typename ST>
 ENS_FN int ens_column(const CavDesc &d, int cur, int inflight, int phase, int col) {
     if (phase == 2) {
@@ -143,14 +154,16 @@ ENS_FN int ens_column(const CavDesc &d, int cur, int inflight, int phase, int co
 }
 
 template <typename ST, int K>
-__global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_constant__ EnsWork w, int nsteps) {
+__global__ void ENS_BOUNDS k_ensemble(const __grid_constant__ EnsWork w, int nsteps) {
     const long long items1 = w.item_begin[w.ncav], items2 = w.col_begin[w.ncav];
     __shared__ int top[kMaxCavities];  // per cavity: first height at which every node is deep solid
     __shared__ long long next;         // first item of the block's next chunk
     // per-step item counters (alternating), zeroed with the barrier words
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(w.bar + 4);
     constexpr int kChunk = 1;  // measured: 1, 2, 4 items -> 19.3, 18.7, 18.5 k MLUPS
+    int kc = 0;  // cavity of the block's last item (items are handed out in increasing order)
     for (int t = 0; t < nsteps; ++t) {
+        kc = 0;
         for (int k = threadIdx.x; k < w.ncav; k += blockDim.x) {
             const CavDesc &d = w.desc[k];
             top[k] = d.cut ? *(volatile int *)d.jmax + 3 : 1 << 30;
@@ -168,7 +181,8 @@ __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_con
             if (threadIdx.x == 0) next = (long long)atomicAdd(ctr + (t & 1), (unsigned long long)kChunk);
             const long long stop = base + kChunk < items1 ? base + kChunk : items1;
             for (long long it = base; it < stop; ++it) {
-            const int k = find_cavity(w.item_begin, w.ncav, it);
+            if (it >= w.item_begin[kc + 1]) kc += find_cavity(w.item_begin + kc, w.ncav - kc, it);
+            const int k = kc;
             const CavDesc &d = w.desc[k];
             const int li = (int)(it - w.item_begin[k]);
             const int zc = li / d.gxy, r = li - zc * d.gxy;
@@ -198,7 +212,11 @@ __global__ void __launch_bounds__(256, LBM_ENS_MINB) k_ensemble(const __grid_con
         // step before, which every block has left
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(t + 1) & 1] = 0ull;
         if (!grid_barrier(w, gridDim.x)) return;
-        // phases 2 and 3: front update (Eq. 6), then flip, of every column
+        // phases 2 and 3: front update (Eq. 6), then flip, of every column.
+        // Items are dealt round-robin: consecutive items, which hold
+        // neighbouring columns and so much the same amount of flip work, go
+        // to different blocks (one contiguous range per block ran the flip
+        // phase 67 against 37 us a step on the 48-cavity workload).
         for (int phase = 2; phase <= 3; ++phase) {
             for (long long it = blockIdx.x; it < items2; it += gridDim.x) {
                 const int k = find_cavity(w.col_begin, w.ncav, it);

@@ -957,6 +957,54 @@ __global__ void __launch_bounds__(128) k_front_cond(const __grid_constant__ KP p
 // Every column also records the minimum and maximum of the new liquid counts
 // over its 3x3 neighbourhood (min << 16 | max) for the interior and
 // deep-solid tests of the next stream-collide.  do_flip = 0 only records.
+// The links I0 .. I0 + 8 of a flipped node c = (x, y, z) (see flip_column).
+// The 18 links of one node touch 36 distinct slots (slot i of c, slot opp(i)
+// of c - e_i), so every phase flag and slot of the nine is loaded before the
+// first store: the loads are in flight together, where a link-by-link loop
+// waits two dependent memory round trips per link (the compiler cannot move
+// a load above a store into the same array).  Same values, same stores.
+template <typename ST, int FACE, int I0>
+__device__ __forceinline__ void flip_links(const KP &p, ST *__restrict__ F, const int *__restrict__ js_old,
+                                           const int *__restrict__ js_new, int x, int y, int z, long long c,
+                                           bool lx_t, bool lx_n) {
+    bool yin[9], ly_t[9], ly_n[9], own[9];
+    long long cy[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = I0 + k;
+        const int xn = x - ex(i), yn = y - ey(i), zn = z - ez(i);
+        yin[k] = inside(p, xn, yn, zn);
+        ly_t[k] = ly_n[k] = false;
+        cy[k] = 0;
+        if (yin[k]) {
+            const int cc = column<FACE>(p, xn, yn, zn), an = axial<FACE>(xn, yn, zn);
+            ly_t[k] = an < js_old[cc];
+            ly_n[k] = an < js_new[cc];
+            cy[k] = node_index(p, xn, yn, zn);
+        }
+        own[k] = !(ly_t[k] != ly_n[k] && cy[k] < c);  // else the other end owns this link
+    }
+    float P[9], Q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = I0 + k;
+        P[k] = own[k] && yin[k] ? Store<ST>::ld(F + opp(i) * p.ld + cy[k]) : 0.0f;
+        Q[k] = own[k] ? Store<ST>::ld(F + i * p.ld + c) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        if (!own[k]) continue;
+        const int i = I0 + k;
+        ST *Ps = F + opp(i) * p.ld + cy[k];
+        ST *Qs = F + i * p.ld + c;
+        const float dx = !lx_t ? 0.0f : (ly_t[k] ? P[k] : Q[k]);
+        const float dy = !ly_t[k] ? 0.0f : (lx_t ? Q[k] : P[k]);
+        if (lx_n && ly_n[k]) { Store<ST>::st(Ps, dx); Store<ST>::st(Qs, dy); }
+        else if (lx_n) Store<ST>::st(Qs, dx);
+        else if (ly_n[k]) Store<ST>::st(Ps, dy);
+    }
+}
+
 template <typename ST, int FACE>
 __device__ __forceinline__ void flip_column(const KP &p, ST *__restrict__ F, const int *__restrict__ js_old,
                                           const int *__restrict__ js_new, int *__restrict__ nb_new, int inflight,
@@ -988,33 +1036,15 @@ __device__ __forceinline__ void flip_column(const KP &p, ST *__restrict__ F, con
             continue;
         }
         if (lx_n && !lx_t) Store<ST>::st(F + c, 0.0f);
-        for (int i = 1; i < 19; ++i) {
-            const int xn = x - ex(i), yn = y - ey(i), zn = z - ez(i);
-            const bool yin = inside(p, xn, yn, zn);
-            bool ly_t = false, ly_n = false;
-            long long cy = 0;
-            if (yin) {
-                const int cc = column<FACE>(p, xn, yn, zn), an = axial<FACE>(xn, yn, zn);
-                ly_t = an < js_old[cc];
-                ly_n = an < js_new[cc];
-                cy = node_index(p, xn, yn, zn);
-                if (ly_t != ly_n && cy < c) continue;  // the other end owns this link
-            }
-            ST *Ps = F + opp(i) * p.ld + cy;
-            ST *Qs = F + i * p.ld + c;
-            const float P = yin ? Store<ST>::ld(Ps) : 0.0f;
-            const float Q = Store<ST>::ld(Qs);
-            const float dx = !lx_t ? 0.0f : (ly_t ? P : Q);
-            const float dy = !ly_t ? 0.0f : (lx_t ? Q : P);
-            if (lx_n && ly_n) { Store<ST>::st(Ps, dx); Store<ST>::st(Qs, dy); }
-            else if (lx_n) Store<ST>::st(Qs, dx);
-            else if (ly_n) Store<ST>::st(Ps, dy);
-        }
+        flip_links<ST, FACE, 1>(p, F, js_old, js_new, x, y, z, c, lx_t, lx_n);
+        flip_links<ST, FACE, 10>(p, F, js_old, js_new, x, y, z, c, lx_t, lx_n);
     }
 }
 
+// 4 blocks of 128 a multiprocessor (up to 128 registers: flip_links holds
+// nine links' flags and slots; 608 blocks cover a 256 x 256 front at once).
 template <typename ST, int FACE>
-__global__ void __launch_bounds__(128) k_flip(const __grid_constant__ KP p, ST *__restrict__ F, const int *__restrict__ js_old,
+__global__ void __launch_bounds__(128, 4) k_flip(const __grid_constant__ KP p, ST *__restrict__ F, const int *__restrict__ js_old,
                                               const int *__restrict__ js_new, int *__restrict__ nb_new,
                                               int inflight, int do_flip) {
     step_launch_wait();
