@@ -595,7 +595,9 @@ def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
     or graph-replayed launches) over seq_steps.  MLUPS count liquid
     node-updates (liquid counts averaged over each run); the roofline
     fraction is the ensemble's whole step (all three phases) against the
-    stream-collide's 208 B per liquid node (28 B per active solid node)."""
+    stream-collide's 208 B per liquid node (28 B per active solid node), and
+    the same bytes over the stream-collide phase alone (the kernel's own
+    phase timers)."""
     import torch
     from paper_1604_03478_gb300 import Ensemble, autotune, inputs
     stream = torch.cuda.current_stream()
@@ -619,6 +621,7 @@ def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
         return liq, sol
 
     c0 = counts()
+    ens.phase_times(reset=True)
     e0, e1 = _events()
     e0.record(stream)
     ens.step(steps)
@@ -626,6 +629,7 @@ def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
     ens.sync()
     torch.cuda.synchronize()
     ms_ens = e0.elapsed_time(e1)
+    phases = ens.phase_times()
     c1 = counts()
     liq_ens = 0.5 * (c0[0] + c1[0])
     sol_ens = 0.5 * (c0[1] + c1[1])
@@ -642,11 +646,17 @@ def ensemble_leg(steps=10000, seq_steps=1000, n_cav=48, seed=2016):
     mlups = liq_ens * steps / (ms_ens * 1e-3) / 1e6
     seq_mlups = liq_seq * seq_steps / (ms_seq * 1e-3) / 1e6
     gbs = (208.0 * liq_ens + 28.0 * sol_ens) * steps / (ms_ens * 1e-3) / 1e9
+    sc_gbs = (208.0 * liq_ens + 28.0 * sol_ens) / (phases["stream_collide_us"] * 1e-6) / 1e9
     return {"cavities": n_cav, "nodes": info["nodes"], "liquid_nodes": liq_ens, "steps": steps,
             "mlups": mlups, "sequential_mlups": seq_mlups, "sequential_steps": seq_steps,
             "speedup_vs_sequential": mlups / seq_mlups,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "timed": "whole ensemble step (stream-collide, front and flip phases with their barriers)"},
+            "phases_us_per_step": phases,
+            "stream_collide_phase_roofline": {
+                "bound": "hbm", "achieved": sc_gbs, "peak": peak, "unit": "GB/s", "frac": sc_gbs / peak,
+                "timed": "phase 1 alone (the fused stream-collide of every cavity, up to block 0 leaving its "
+                         "closing grid barrier), on the GPU's global timer"},
             "launch": {"block": shape[0], "nodes_per_thread": shape[1]},
             "workload": "sizes uniform in {48,64,96,128,160}, Ra log-uniform [1e4,1e6], Ste U[0.05,0.2], "
                         "Pr 0.02, heated face y0 or z0, seed %d, front at 0.4 H, FP32" % seed}

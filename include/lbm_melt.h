@@ -372,6 +372,18 @@ lbm_status lbm_ensemble_set_barrier_timeout(lbm_ensemble *e, long long max_spins
    The members' states are not meaningful afterwards. */
 lbm_status lbm_ensemble_inject_barrier_fault(lbm_ensemble *e, int block);
 
+/* Phase timers of the persistent kernel: block 0 reads the GPU's global
+   timer each time it leaves a grid barrier, so a step splits into the fused
+   stream-collide of every cavity (phase 1), the front update of every column
+   (Eq. 6, phase 2) and the phase flip (phase 3), each with the barrier that
+   ends it.  us_per_step (3 doubles, may be NULL): the mean microseconds per
+   step of each phase since the ensemble was created or last reset; steps
+   (may be NULL): the steps timed.  reset != 0 zeroes the timers after the
+   read.  Synchronizes the ensemble's stream (call it between steps, not
+   while a capture is open).  LBM_EINVAL for a NULL ensemble, LBM_ECUDA if
+   the read fails. */
+lbm_status lbm_ensemble_phase_times(lbm_ensemble *e, int reset, double *us_per_step, long long *steps);
+
 /* Wait for the ensemble; report a barrier timeout or a member's error. */
 lbm_status lbm_ensemble_sync(lbm_ensemble *e);
 

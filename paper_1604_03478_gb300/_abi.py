@@ -97,6 +97,7 @@ def load() -> C.CDLL:
         "lbm_ensemble_member": (vp, [vp, C.c_int]),
         "lbm_ensemble_info": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]),
+        "lbm_ensemble_phase_times": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "lbm_ensemble_last_error": (C.c_char_p, [vp]),
         "lbm_ensemble_destroy": (None, [vp]),
         "lbm_melt_destroy": (None, [vp]),

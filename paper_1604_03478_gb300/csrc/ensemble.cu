@@ -244,7 +244,10 @@ LBM_API lbm_status lbm_ensemble_create(int n, const lbm_melt_case *cases, void *
         if (k == 0) e->precision = h->precision;
         else if (h->precision != e->precision) return fail(LBM_EINVAL);
     }
-    if (cudaMalloc(&e->bar_dev, 8 * sizeof(unsigned int)) != cudaSuccess) return fail(LBM_ENOMEM);
+    // 8 barrier words, then the phase timers (4 x u64), zeroed here only
+    if (cudaMalloc(&e->bar_dev, 16 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(e->bar_dev, 0, 16 * sizeof(unsigned int)) != cudaSuccess)
+        return fail(LBM_ENOMEM);
     refresh_desc(e);
     if (plan(e) != LBM_OK) return fail(LBM_ECUDA);
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) return fail(LBM_ECUDA);
@@ -355,6 +358,18 @@ LBM_API lbm_status lbm_ensemble_sync(lbm_ensemble *e) {
         lbm_status st = lbm_melt_sync(e->cav[k]);
         if (st != LBM_OK) return ens_err(e, st, "cavity %d: %s", k, lbm_melt_last_error(e->cav[k]));
     }
+    return LBM_OK;
+}
+
+LBM_API lbm_status lbm_ensemble_phase_times(lbm_ensemble *e, int reset, double *us_per_step, long long *steps) {
+    if (!e) return LBM_EINVAL;
+    unsigned long long acc[4] = {0, 0, 0, 0};
+    ECK(cudaMemcpyAsync(acc, e->bar_dev + 8, sizeof acc, cudaMemcpyDeviceToHost, e->stream), "timer read");
+    if (reset) ECK(cudaMemsetAsync(e->bar_dev + 8, 0, sizeof acc, e->stream), "timer reset");
+    ECK(cudaStreamSynchronize(e->stream), "synchronize");
+    if (us_per_step)
+        for (int i = 0; i < 3; ++i) us_per_step[i] = acc[3] ? (double)acc[i] * 1e-3 / (double)acc[3] : 0.0;
+    if (steps) *steps = (long long)acc[3];
     return LBM_OK;
 }
 

@@ -60,7 +60,8 @@ struct EnsWork {
     long long item_begin[kMaxCavities + 1];  // prefix sums of node items
     long long col_begin[kMaxCavities + 1];   // prefix sums of column items
     CavDesc desc[kMaxCavities];
-    unsigned int *bar;            // {arrived, generation, timed out, -, item counters (2 x u64)}
+    unsigned int *bar;            // {arrived, generation, timed out, -, item counters (2 x u64),
+                                  //  phase times in ns and steps (4 x u64)}
     long long max_spins;
     int skip_arrival_block;       // fault injection for tests: this block never arrives (-1: none)
 };
@@ -106,6 +107,12 @@ __device__ __forceinline__ bool grid_barrier(const EnsWork &w, unsigned int nblo
     }
     __syncthreads();
     return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ int find_cavity(const long long *begin, int n, long long item) {
@@ -162,6 +169,12 @@ __global__ void ENS_BOUNDS k_ensemble(const __grid_constant__ EnsWork w, int nst
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(w.bar + 4);
     constexpr int kChunk = 1;  // measured: 1, 2, 4 items -> 19.3, 18.7, 18.5 k MLUPS
     int kc = 0;  // cavity of the block's last item (items are handed out in increasing order)
+    // Block 0 times the phases on the global timer: each phase ends when
+    // block 0 leaves the grid barrier after it (accumulated, with the step
+    // count, in the barrier words 8..15 for lbm_ensemble_phase_times).
+    unsigned long long *phase_ns = reinterpret_cast<unsigned long long *>(w.bar + 8);
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tp = timer ? global_ns() : 0ull;
     for (int t = 0; t < nsteps; ++t) {
         kc = 0;
         for (int k = threadIdx.x; k < w.ncav; k += blockDim.x) {
@@ -212,6 +225,7 @@ __global__ void ENS_BOUNDS k_ensemble(const __grid_constant__ EnsWork w, int nst
         // step before, which every block has left
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(t + 1) & 1] = 0ull;
         if (!grid_barrier(w, gridDim.x)) return;
+        if (timer) { const unsigned long long tn = global_ns(); phase_ns[0] += tn - tp; tp = tn; }
         // phases 2 and 3: front update (Eq. 6), then flip, of every column.
         // Items are dealt round-robin: consecutive items, which hold
         // neighbouring columns and so much the same amount of flip work, go
@@ -230,6 +244,12 @@ __global__ void ENS_BOUNDS k_ensemble(const __grid_constant__ EnsWork w, int nst
                 }
             }
             if (!grid_barrier(w, gridDim.x)) return;
+            if (timer) {
+                const unsigned long long tn = global_ns();
+                phase_ns[phase - 1] += tn - tp;
+                tp = tn;
+                if (phase == 3) phase_ns[3] += 1ull;
+            }
         }
     }
 }

@@ -69,6 +69,15 @@ class Ensemble:
         self._check(_abi.load().lbm_ensemble_info(self._h, C.byref(n), C.byref(g), C.byref(b), C.byref(k)))
         return dict(nodes=n.value, grid=g.value, block=b.value, nodes_per_thread=k.value)
 
+    def phase_times(self, reset=False):
+        """Mean microseconds per step of the stream-collide, front and flip
+        phases (each with its closing grid barrier) since creation or the
+        last reset, and the number of steps timed."""
+        us = (C.c_double * 3)()
+        n = C.c_longlong()
+        self._check(_abi.load().lbm_ensemble_phase_times(self._h, 1 if reset else 0, us, C.byref(n)))
+        return dict(stream_collide_us=us[0], front_us=us[1], flip_us=us[2], steps=n.value)
+
     def member(self, i):
         h = _abi.load().lbm_ensemble_member(self._h, int(i))
         if not h:

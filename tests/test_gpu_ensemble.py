@@ -112,6 +112,33 @@ def test_ensemble_then_member_steps(pkg):
     ens.close()
 
 
+def test_phase_timers(pkg):
+    """The persistent kernel's phase timers: every timed step is counted,
+    each phase takes time, the three add up to no more than the step's
+    wall time measured with CUDA events, and a reset zeroes them."""
+    import torch
+    ens = pkg.Ensemble(CASES)
+    ens.step(4)
+    ens.sync()
+    ens.phase_times(reset=True)
+    z = ens.phase_times()
+    assert z["steps"] == 0 and z["stream_collide_us"] == 0.0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(40)
+    e1.record(stream)
+    ens.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph = ens.phase_times()
+    assert ph["steps"] == 40
+    parts = [ph["stream_collide_us"], ph["front_us"], ph["flip_us"]]
+    assert all(v > 0.0 for v in parts)
+    assert sum(parts) * 40 <= ms * 1e3 * 1.02 + 20.0  # timer ticks: the parts telescope per launch
+    ens.close()
+
+
 def test_barrier_timeout_is_reported(pkg):
     """Failure detection: block 0 never arrives at the first barrier; every
     other block's bounded wait runs out, the launch returns, the host reads
