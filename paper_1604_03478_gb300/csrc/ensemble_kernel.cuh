@@ -124,9 +124,9 @@ __device__ __forceinline__ int find_cavity(const long long *begin, int n, long l
     return lo;
 }
 
-// One node of phase 1.  Each (face, parity) variant is its own out-of-line
-// function so that the variants do not share one register allocation.  The
-// even step indexes in 32 bits (lbm_ensemble_create admits members whose
+// One node of phase 1, one function per (face, parity) variant (inlined;
+// out of line, so that the variants do not share one register allocation,
+// when LBM_ENS_NOINLINE is set).  The even step indexes in 32 bits (lbm_ensemble_create admits members whose
 // indices fit): 23.4 k against 22.8 k MLUPS over 1000 steps of the 48-cavity
 // workload.
 template <typename ST, int FACE>
