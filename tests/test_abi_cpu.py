@@ -93,3 +93,28 @@ def test_workload_lattice_parameters(abi):
     assert st == st2 == abi.LBM_OK
     assert i128.nu == pytest.approx(3.30e-3, rel=3e-3) and i128.tau_nu == pytest.approx(0.5099, abs=1e-4)
     assert i256.nu == pytest.approx(2.09e-3, rel=3e-3) and i256.tau_nu == pytest.approx(0.5063, abs=1e-4)
+
+
+NULL_HANDLE_CALLS = [
+    ("lbm_melt_step", (1,)), ("lbm_melt_sync", ()), ("lbm_melt_totals", (None, 0)),
+    ("lbm_melt_set_report", (0, 0)), ("lbm_melt_get_report", (None, 0, None)),
+    ("lbm_melt_get", (None, None, None, None, 0)), ("lbm_melt_get_async", (None, None, 0)),
+    ("lbm_melt_get_noalloc", (None, None, None, None, 0)), ("lbm_melt_get_state", (None, None, None, 0)),
+    ("lbm_melt_set_state", (None, None, None, 0)), ("lbm_melt_set_hot_wall", (None, 0)),
+    ("lbm_melt_get_nusselt", (None, None, 0)), ("lbm_melt_get_info", (None,)), ("lbm_melt_set_launch", (128, 1)),
+    ("lbm_melt_set_graph_steps", (16,)), ("lbm_melt_set_node_pairs", (0,)),
+    ("lbm_melt_set_solid_conduction", (1.0,)), ("lbm_melt_set_timing", (1,)),
+    ("lbm_melt_kernel_time", (None, None, 0)), ("lbm_melt_tape_forward", (10, 0)), ("lbm_melt_tape_clear", ()),
+    ("lbm_melt_tape_backward", (None, None, None, 0)),
+    ("lbm_ensemble_step", (1,)), ("lbm_ensemble_sync", ()), ("lbm_ensemble_set_launch", (128, 2, 8)),
+    ("lbm_ensemble_set_barrier_timeout", (1000,)), ("lbm_ensemble_inject_barrier_fault", (0,)),
+    ("lbm_ensemble_phase_times", (0, None, None)), ("lbm_ensemble_info", (None, None, None, None)),
+]
+
+
+@pytest.mark.parametrize("name,args", NULL_HANDLE_CALLS, ids=[c[0] for c in NULL_HANDLE_CALLS])
+def test_null_handle_is_rejected(abi, name, args):
+    """Every entry point that takes a handle answers LBM_EINVAL for a NULL one
+    and touches nothing else (no GPU needed)."""
+    fn = getattr(abi.load(), name)
+    assert fn(None, *args) == abi.LBM_EINVAL
